@@ -1,0 +1,52 @@
+"""Pins of the oracle's MLP: backward pass and input tangent against finite differences, one Adam step by hand."""
+import numpy as np
+
+from oracle import mlp
+
+
+def _setup(seed=0, H=8, F=5, B=7):
+    rng = np.random.default_rng(seed)
+    params = mlp.init_params(H, F, rng)
+    params["b2"] = rng.standard_normal(H) * 0.3
+    params["b3"] = rng.standard_normal(F) * 0.3
+    t = rng.random(B)
+    target = rng.standard_normal((B, F))
+    return params, t, target
+
+
+def test_backward_matches_finite_differences():
+    params, t, target = _setup()
+    loss, g = mlp.loss_and_grads(params, t, target)
+    h = 1e-6
+    for k, v in params.items():
+        flat = v.reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 9)):
+            p1 = {kk: vv.copy() for kk, vv in params.items()}
+            p2 = {kk: vv.copy() for kk, vv in params.items()}
+            p1[k].reshape(-1)[idx] += h
+            p2[k].reshape(-1)[idx] -= h
+            fd = (mlp.loss_and_grads(p1, t, target)[0] - mlp.loss_and_grads(p2, t, target)[0]) / (2 * h)
+            assert abs(fd - g[k].reshape(-1)[idx]) < 1e-7 * max(1.0, abs(fd)), (k, idx)
+
+
+def test_input_tangent_matches_finite_differences():
+    params, t, _ = _setup(1)
+    _, dy, _ = mlp.forward(params, t, tangent=True)
+    h = 1e-6
+    fd = (mlp.forward(params, t + h)[0] - mlp.forward(params, t - h)[0]) / (2 * h)
+    assert np.allclose(dy, fd, atol=1e-8)
+
+
+def test_silu_derivative():
+    z = np.linspace(-6, 6, 101)
+    h = 1e-6
+    assert np.allclose(mlp.silu_grad(z), (mlp.silu(z + h) - mlp.silu(z - h)) / (2 * h), atol=1e-9)
+
+
+def test_first_adam_step_is_lr_times_sign():
+    # with bias correction, the first step is lr * g / (|g| + eps)
+    params, t, target = _setup(2)
+    _, g = mlp.loss_and_grads(params, t, target)
+    new = mlp.adam_step({k: v.copy() for k, v in params.items()}, g, {}, lr=1e-3)
+    for k in params:
+        assert np.allclose(params[k] - new[k], 1e-3 * g[k] / (np.abs(g[k]) + 1e-8), atol=1e-15)
