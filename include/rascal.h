@@ -1,0 +1,171 @@
+/*
+ * rascal.h - C ABI of the GB300 (sm_103a) SOAP density-expansion library.
+ *
+ * What it computes (arXiv:2101.08814):
+ *   neighbours      every (i, j, n) with |r_j - r_i + n1 h1 + n2 h2 + n3 h3| < r_cut, periodic images included
+ *                   (Appendix B: "r_ji < r_cut", j over periodic replicas)
+ *   expansion       c^i_{a n l m} = sum_{j in A_i, a_j = a} f_cut(r_ji) I^o_nl(r_ji) Y_lm(r^_ji)
+ *                   (Eq. spherical_expansion_coefficients_gaussians; I^o is the o-GTO radial integral of
+ *                   Eq. rad-int-gto-1 orthogonalised with S^-1/2, Sec. 'GTO radial basis'; Y_lm real spherical
+ *                   harmonics, Sec. 'Spherical Harmonics'; radial values from a cubic spline, Sec. 'Spline optimization')
+ *   power spectrum  p^i_{(a1 n1)(a2 n2) l} = (2l+1)^-1/2 sum_m c^i_{a1 n1 l m} c^i_{a2 n2 l m}  (Eq. nu2-basis-coupled)
+ *   gradients       forces -dE/dr_k and virial sum_ij dE/dr_ji (x) r_ji of E = sum_i G_i . p_i
+ *                   (Eqs. energy-derivative and energy-virial, Appendix B)
+ *
+ * Conventions shared by every call:
+ *   - Lengths are in Angstrom. Positions are [N][3] float64 and are used as given (not wrapped).
+ *   - Cells are [n_structures][3][3] float64, row k is the cell vector h_{k+1}.
+ *   - Species are integer labels (e.g. atomic numbers, 0..255). rascal_hypers.species lists the labels in use;
+ *     the species index a of a label is its rank in the sorted list. Combined radial/species index q = a*n_max + n.
+ *   - c is float32 [n_centres][n_species][n_max][(l_max+1)^2] with lm = l*l + l + m, m = -l..l.
+ *   - p PACKED is float32 [n_centres][l_max+1][Q(Q+1)/2], Q = n_species*n_max, pairs q1 <= q2 row-major;
+ *     p FULL is float32 [n_centres][l_max+1][Q][Q].
+ *   - Every device pointer argument ("d_") is caller-owned device memory; the library only borrows it for the
+ *     duration of the call. The context owns the radial table, its scratch arena and the MLP weights.
+ *   - All work is enqueued on the context's CUDA stream. Calls that must read a count from the device
+ *     (rascal_neighbours) synchronise that stream; the others return as soon as the work is enqueued.
+ *   - Every call returns RASCAL_OK (0) or a negative RASCAL_E_* status; rascal_last_error() then holds a
+ *     message for the calling thread. No call aborts the process.
+ */
+#ifndef RASCAL_H
+#define RASCAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RASCAL_OK 0
+#define RASCAL_E_ARG (-1)         /* invalid argument (null pointer, out-of-range hyper, unknown species) */
+#define RASCAL_E_CAPACITY (-2)    /* output buffer too small; the required size is reported */
+#define RASCAL_E_CUDA (-3)        /* a CUDA runtime call failed */
+#define RASCAL_E_UNSUPPORTED (-4) /* valid input outside what the kernels support (e.g. |shift| > 511) */
+#define RASCAL_E_GEOMETRY (-5)    /* degenerate geometry: singular cell, coincident atoms (r < 1e-6 A) */
+#define RASCAL_E_NOMEM (-7)       /* device allocation of context scratch failed */
+
+/* radial integral source */
+#define RASCAL_RADIAL_SPLINE 0 /* FP32 cubic spline of the FP64 o-GTO integrals (default) */
+#define RASCAL_RADIAL_EXACT 1  /* per-pair 1F1 series/asymptotic + recurrence, FP32 */
+#define RASCAL_RADIAL_MLP 2    /* the trained MLP surrogate held by the context */
+
+/* power-spectrum arithmetic */
+#define RASCAL_PS_FP32 0 /* FP32 inputs and accumulation (CUDA cores) */
+#define RASCAL_PS_BF16 1 /* BF16 inputs, FP32 accumulation (tcgen05 tensor cores) */
+
+/* power-spectrum layout */
+#define RASCAL_LAYOUT_PACKED 0
+#define RASCAL_LAYOUT_FULL 1
+
+/* Expansion parameters (paper notation). Limits: 1 <= n_max <= 32, 0 <= l_max <= 15, 1 <= n_species <= 16,
+ * n_species*n_max <= 256, 0 < smooth_width <= r_cut, sigma > 0. */
+typedef struct {
+    double r_cut;            /* cutoff radius r_cut, Angstrom */
+    double smooth_width;     /* width w of the cosine cutoff f_cut: 1 below r_cut - w, 0 at r_cut */
+    double sigma;            /* Gaussian width sigma of the atom density; c = 1/(2 sigma^2) */
+    int n_max;               /* radial functions n = 0..n_max-1 */
+    int l_max;               /* angular channels l = 0..l_max */
+    int n_species;           /* number of species labels in `species` */
+    const int* species;      /* HOST pointer, n_species distinct labels in 0..255, any order */
+    int radial;              /* RASCAL_RADIAL_* */
+    int orthonormal;         /* 1: o-GTO basis (S^-1/2 applied in FP64), 0: raw GTO */
+    int include_center;      /* 1: the centre adds its own r = 0 term to its species block */
+    int ps_norm;             /* 1: keep the (2l+1)^-1/2 factor of Eq. nu2-basis-coupled */
+    double spline_accuracy;  /* target max |spline - exact| at interval midpoints (FP64 build); <= 0: 1e-8 */
+    int spline_intervals;    /* > 0: force this many intervals M; 0: double M from 64 until the accuracy holds */
+} rascal_hypers;
+
+/* Structures in device memory. Atoms of structure s are struct_offsets[s] .. struct_offsets[s+1]-1. */
+typedef struct {
+    int n_structures;
+    int n_atoms;
+    const int* d_struct_offsets; /* [n_structures+1] int32 */
+    const double* d_positions;   /* [n_atoms][3] float64 */
+    const double* d_cells;       /* [n_structures][3][3] float64, rows h1, h2, h3 */
+    const int* d_pbc;            /* [n_structures][3] int32, 1 = periodic along h_k; NULL = all periodic */
+    const int* d_species;        /* [n_atoms] int32 labels */
+} rascal_system;
+
+typedef struct rascal_ctx rascal_ctx;
+
+/* Sizes derived from the hypers (filled by rascal_info). */
+typedef struct {
+    int n_species, n_max, l_max;
+    int n_lm;                    /* (l_max+1)^2 */
+    int64_t coeffs_per_centre;   /* n_species*n_max*n_lm */
+    int64_t features_packed;     /* (l_max+1)*Q(Q+1)/2 */
+    int64_t features_full;       /* (l_max+1)*Q*Q */
+    int spline_intervals;        /* M chosen for the radial table */
+    double spline_error;         /* max |FP64 spline - exact| at interval midpoints, over all (n, l) */
+    double spline_error_fp32;    /* the same for the FP32 coefficients the kernels read */
+} rascal_info_t;
+
+/* Thread-local message of the last failed call on this thread ("" if none). Never NULL. */
+const char* rascal_last_error(void);
+
+/* Build a context: validates the hypers, computes the GTO constants and the FP64 overlap matrix with its
+ * inverse square root (Sec. 'GTO radial basis'), tabulates the o-GTO radial integrals in FP64 on the GPU with
+ * the series/asymptotic 1F1 of Appendix A, solves the clamped cubic spline and stores FP32 per-interval
+ * coefficients. `cuda_stream` is a cudaStream_t (NULL = legacy default stream). Synchronises the stream. */
+int rascal_create(const rascal_hypers* hypers, void* cuda_stream, rascal_ctx** out);
+void rascal_destroy(rascal_ctx* ctx);
+int rascal_set_stream(rascal_ctx* ctx, void* cuda_stream);
+int rascal_info(const rascal_ctx* ctx, rascal_info_t* out);
+
+/* Synchronises the context stream and turns device-side error flags raised by earlier calls (unknown species
+ * label, degenerate geometry, ...) into a status. */
+int rascal_sync(rascal_ctx* ctx);
+
+/* Periodic neighbour list (Appendix B). For every atom i (all structures, in atom order) the pairs (j, n) with
+ * |r_j - r_i + n H| < r_cut, (j, n) != (i, 0), sorted by (j, n1, n2, n3). The inclusion test is bit-exact with
+ * the FP64 definition d = (r_j - r_i) + ((n1 h1 + n2 h2) + n3 h3), d.d = (dx dx + dy dy) + dz dz < r_cut^2.
+ *   d_offsets [n_atoms+1] int64: CSR offsets (written whenever the call gets as far as counting)
+ *   d_nbr_j   [capacity] int32: neighbour atom index (global numbering)
+ *   d_shift   [capacity][3] int32: n
+ *   d_rij     [capacity][4] float32: (x, y, z, |r_ji|) of r_ji = r_j - r_i + n H, accurate to FP32 rounding
+ *   n_pairs   host out: the number of pairs P
+ * If P > capacity the call returns RASCAL_E_CAPACITY with *n_pairs = P and leaves the pair arrays unwritten.
+ * Synchronises the stream once (to read P). Cells with a perpendicular width below r_cut/64 return
+ * RASCAL_E_UNSUPPORTED. */
+int rascal_neighbours(rascal_ctx* ctx, const rascal_system* sys, int64_t capacity, int64_t* d_offsets,
+                      int* d_nbr_j, int* d_shift, float* d_rij, int64_t* n_pairs);
+
+/* Spherical expansion coefficients (Eq. spherical_expansion_coefficients_gaussians) of every centre from a pair
+ * list made by rascal_neighbours for the same system. d_coeffs: [n_atoms][n_species][n_max][(l_max+1)^2]. */
+int rascal_spherical_expansion(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets,
+                               const int* d_nbr_j, const float* d_rij, float* d_coeffs);
+
+/* Power spectrum (Eq. nu2-basis-coupled) of n_centres coefficient blocks. precision: RASCAL_PS_FP32 or
+ * RASCAL_PS_BF16 (tensor cores, inputs rounded to bfloat16, FP32 accumulation). layout: RASCAL_LAYOUT_*. */
+int rascal_power_spectrum(rascal_ctx* ctx, int64_t n_centres, const float* d_coeffs, int precision, int layout,
+                          float* d_ps);
+
+/* Expansion and power spectrum in one pass: c is written to d_coeffs and p to d_ps (FP32 arithmetic). */
+int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,
+                const float* d_rij, int layout, float* d_coeffs, float* d_ps);
+
+/* Per-structure energy of the additive linear model E = sum_i w_{a_i} . p_i (Eq. additive-energy-model) from
+ * PACKED p: d_weights [n_species][features_packed] float32, d_energy [n_structures] float64 (overwritten). */
+int rascal_linear_energy(rascal_ctx* ctx, const rascal_system* sys, const float* d_ps_packed,
+                         const float* d_weights, double* d_energy);
+
+/* Gradients of E = sum_i G_i . p_i (PACKED p) with respect to the positions and the cell (Appendix B).
+ * Exactly one of d_grad_ps ([n_atoms][features_packed], G_i per centre) or d_weights ([n_species]
+ * [features_packed], G_i = w_{a_i}, the linear model) must be non-NULL. The pair terms are recomputed per pair
+ * from the spline and Y_lm; dc/dr is never stored.
+ *   d_forces [n_atoms][3] float64: overwritten with F_k = -dE/dr_k (images of the centre add nothing)
+ *   d_virial [n_structures][9] float64: overwritten with V[a][b] = sum_pairs dE/dr_ji[a] r_ji[b] */
+int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,
+                     const float* d_rij, const float* d_coeffs, const float* d_grad_ps, const float* d_weights,
+                     double* d_forces, double* d_virial);
+
+/* Exact FP64 o-GTO radial integrals I^o_nl(r) and their r-derivatives at n_points distances (Eq. rad-int-gto-1
+ * with the 1F1 of Appendix A, then S^-1/2): d_r [n] float64, d_out and d_dout [n][n_max][l_max+1] float64
+ * (d_dout may be NULL). Used to build the spline and the MLP training targets. */
+int rascal_radial_exact_fp64(rascal_ctx* ctx, int64_t n_points, const double* d_r, double* d_out, double* d_dout);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RASCAL_H */

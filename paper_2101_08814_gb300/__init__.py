@@ -1,0 +1,206 @@
+"""GB300 (sm_103a) SOAP density expansion of arXiv:2101.08814 behind a C ABI (include/rascal.h).
+
+This module is the thin Python binding: it allocates output tensors with PyTorch, passes device pointers and the
+current CUDA stream to the library, and turns status codes into exceptions. Every step of the computation runs
+in the library's CUDA kernels; there is no CPU path. Importing works without a GPU; creating a calculator needs
+the built library and a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+from . import _lib
+from ._lib import LAYOUT, PRECISION, RADIAL, RascalError  # noqa: F401
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+@dataclass
+class DeviceSystem:
+    """Structures resident on the GPU (tensors kept alive for the duration of the calls)."""
+
+    positions: "object"       # torch.float64 [N, 3]
+    species: "object"         # torch.int32 [N]
+    cells: "object"           # torch.float64 [n_s, 3, 3]
+    pbc: "object"             # torch.int32 [n_s, 3]
+    struct_offsets: "object"  # torch.int32 [n_s + 1]
+
+    @property
+    def n_atoms(self):
+        return int(self.positions.shape[0])
+
+    @property
+    def n_structures(self):
+        return int(self.cells.shape[0])
+
+    def c_struct(self):
+        return _lib.System(self.n_structures, self.n_atoms, self.struct_offsets.data_ptr(), self.positions.data_ptr(),
+                           self.cells.data_ptr(), self.pbc.data_ptr(), self.species.data_ptr())
+
+    @staticmethod
+    def from_numpy(system, device="cuda"):
+        import torch
+
+        return DeviceSystem(
+            torch.as_tensor(system.positions, dtype=torch.float64, device=device).contiguous(),
+            torch.as_tensor(system.species, dtype=torch.int32, device=device).contiguous(),
+            torch.as_tensor(system.cells, dtype=torch.float64, device=device).contiguous(),
+            torch.as_tensor(system.pbc, dtype=torch.int32, device=device).contiguous(),
+            torch.as_tensor(system.struct_offsets, dtype=torch.int32, device=device).contiguous(),
+        )
+
+
+@dataclass
+class PairList:
+    offsets: "object"  # int64 [N+1]
+    nbr_j: "object"    # int32 [P]
+    shifts: "object"   # int32 [P, 3]
+    rij: "object"      # float32 [P, 4] (x, y, z, r)
+
+    @property
+    def n_pairs(self):
+        return int(self.nbr_j.shape[0])
+
+
+class SoapCalculator:
+    """Owns one library context (radial spline table and scratch) for a set of hypers."""
+
+    def __init__(self, r_cut, sigma, n_max, l_max, species, smooth_width=0.5, radial="spline", orthonormal=True,
+                 include_center=False, ps_norm=True, spline_accuracy=0.0, spline_intervals=0, device=None, **_ignored):
+        import torch
+
+        self.device = torch.device("cuda" if device is None else device)
+        self.species = sorted(int(s) for s in species)
+        arr = (C.c_int * len(self.species))(*self.species)
+        self._species_arr = arr
+        h = _lib.Hypers(float(r_cut), float(smooth_width), float(sigma), int(n_max), int(l_max), len(self.species),
+                        C.cast(arr, C.POINTER(C.c_int)), RADIAL[radial], int(bool(orthonormal)), int(bool(include_center)),
+                        int(bool(ps_norm)), float(spline_accuracy), int(spline_intervals))
+        self._ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream().cuda_stream
+            _lib.check(_lib.lib().rascal_create(C.byref(h), C.c_void_p(stream), C.byref(self._ctx)))
+        info = _lib.Info()
+        _lib.check(_lib.lib().rascal_info(self._ctx, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in _lib.Info._fields_}
+        self.n_max, self.l_max, self.n_species = int(n_max), int(l_max), len(self.species)
+        self._capacity = 0
+
+    def __del__(self):
+        ctx = getattr(self, "_ctx", None)
+        if ctx is not None and ctx.value:
+            try:
+                _lib.lib().rascal_destroy(ctx)
+            except Exception:
+                pass
+            self._ctx = None
+
+    # ----------------------------------------------------------------------------------------------------------
+    def _bind_stream(self):
+        import torch
+
+        _lib.check(_lib.lib().rascal_set_stream(self._ctx, C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
+
+    @property
+    def coeffs_per_centre(self):
+        return int(self.info["coeffs_per_centre"])
+
+    def n_features(self, layout="packed"):
+        return int(self.info["features_packed" if layout == "packed" else "features_full"])
+
+    def sync(self):
+        self._bind_stream()
+        _lib.check(_lib.lib().rascal_sync(self._ctx))
+
+    def neighbours(self, system: DeviceSystem, capacity=None) -> PairList:
+        import torch
+
+        self._bind_stream()
+        N = system.n_atoms
+        offsets = torch.empty(N + 1, dtype=torch.int64, device=self.device)
+        cap = int(capacity if capacity is not None else max(self._capacity, 64 * N, 1))
+        sys_c = system.c_struct()
+        while True:
+            nbr = torch.empty(cap, dtype=torch.int32, device=self.device)
+            shifts = torch.empty((cap, 3), dtype=torch.int32, device=self.device)
+            rij = torch.empty((cap, 4), dtype=torch.float32, device=self.device)
+            P = C.c_int64(0)
+            st = _lib.lib().rascal_neighbours(self._ctx, C.byref(sys_c), cap, _ptr(offsets), _ptr(nbr), _ptr(shifts),
+                                              _ptr(rij), C.byref(P))
+            if st == _lib.RASCAL_E_CAPACITY:
+                cap = int(P.value * 1.1) + 16
+                continue
+            _lib.check(st)
+            break
+        self._capacity = max(self._capacity, cap)
+        n = int(P.value)
+        return PairList(offsets, nbr[:n], shifts[:n], rij[:n])
+
+    def spherical_expansion(self, system: DeviceSystem, pairs: PairList, out=None):
+        import torch
+
+        self._bind_stream()
+        N = system.n_atoms
+        c = out if out is not None else torch.empty((N, self.n_species, self.n_max, (self.l_max + 1) ** 2),
+                                                    dtype=torch.float32, device=self.device)
+        sys_c = system.c_struct()
+        _lib.check(_lib.lib().rascal_spherical_expansion(self._ctx, C.byref(sys_c), _ptr(pairs.offsets),
+                                                         _ptr(pairs.nbr_j), _ptr(pairs.rij), _ptr(c)))
+        return c
+
+    def power_spectrum(self, coeffs, precision="fp32", layout="packed", out=None):
+        import torch
+
+        self._bind_stream()
+        n = int(coeffs.shape[0])
+        p = out if out is not None else torch.empty((n, self.n_features(layout)), dtype=torch.float32, device=self.device)
+        _lib.check(_lib.lib().rascal_power_spectrum(self._ctx, n, _ptr(coeffs), PRECISION[precision], LAYOUT[layout],
+                                                    _ptr(p)))
+        return p
+
+    def soap(self, system: DeviceSystem, pairs: PairList, layout="packed", coeffs=None, ps=None):
+        import torch
+
+        self._bind_stream()
+        N = system.n_atoms
+        c = coeffs if coeffs is not None else torch.empty((N, self.n_species, self.n_max, (self.l_max + 1) ** 2),
+                                                          dtype=torch.float32, device=self.device)
+        p = ps if ps is not None else torch.empty((N, self.n_features(layout)), dtype=torch.float32, device=self.device)
+        sys_c = system.c_struct()
+        _lib.check(_lib.lib().rascal_soap(self._ctx, C.byref(sys_c), _ptr(pairs.offsets), _ptr(pairs.nbr_j),
+                                          _ptr(pairs.rij), LAYOUT[layout], _ptr(c), _ptr(p)))
+        return c, p
+
+    def linear_energy(self, system: DeviceSystem, ps_packed, weights):
+        import torch
+
+        self._bind_stream()
+        e = torch.empty(system.n_structures, dtype=torch.float64, device=self.device)
+        sys_c = system.c_struct()
+        _lib.check(_lib.lib().rascal_linear_energy(self._ctx, C.byref(sys_c), _ptr(ps_packed), _ptr(weights), _ptr(e)))
+        return e
+
+    def gradients(self, system: DeviceSystem, pairs: PairList, coeffs, grad_ps=None, weights=None):
+        import torch
+
+        self._bind_stream()
+        forces = torch.empty((system.n_atoms, 3), dtype=torch.float64, device=self.device)
+        virial = torch.empty((system.n_structures, 3, 3), dtype=torch.float64, device=self.device)
+        sys_c = system.c_struct()
+        _lib.check(_lib.lib().rascal_gradients(self._ctx, C.byref(sys_c), _ptr(pairs.offsets), _ptr(pairs.nbr_j),
+                                               _ptr(pairs.rij), _ptr(coeffs), _ptr(grad_ps), _ptr(weights),
+                                               _ptr(forces), _ptr(virial)))
+        return forces, virial
+
+    def radial_exact_fp64(self, r, derivative=False):
+        import torch
+
+        self._bind_stream()
+        r = r.to(device=self.device, dtype=torch.float64).contiguous()
+        out = torch.empty((r.shape[0], self.n_max, self.l_max + 1), dtype=torch.float64, device=self.device)
+        dout = torch.empty_like(out) if derivative else None
+        _lib.check(_lib.lib().rascal_radial_exact_fp64(self._ctx, r.shape[0], _ptr(r), _ptr(out), _ptr(dout)))
+        return (out, dout) if derivative else out

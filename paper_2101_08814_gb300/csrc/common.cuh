@@ -1,0 +1,153 @@
+// Internal helpers shared by the library's translation units: status handling, the context, scratch arena and
+// small device utilities. Nothing here is part of the public ABI (include/rascal.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "rascal.h"
+
+namespace rascal {
+
+// -------------------------------------------------------------------------------------------- limits
+constexpr int kMaxNMax = 32;
+constexpr int kMaxLMax = 15;
+constexpr int kMaxSpecies = 16;
+constexpr int kMaxQ = 256;
+constexpr int kMaxShift = 511;  // |n_k| that fits the 10-bit fields of the pair sort key
+
+// device-side error flags (bitwise OR into ctx->d_flags)
+enum : unsigned {
+    kFlagSpecies = 1u << 0,     // an atom's label is not in the hypers' species list
+    kFlagGeometry = 1u << 1,    // singular cell or coincident atoms
+    kFlagThinCell = 1u << 2,    // perpendicular cell width below r_cut / 64
+    kFlagShiftRange = 1u << 3,  // |n_k| above kMaxShift
+    kFlagBadOffsets = 1u << 4,  // structure offsets not increasing / out of range
+};
+
+// -------------------------------------------------------------------------------------------- status
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+#define RASCAL_CUDA(call)                                                                               \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return ::rascal::set_error(RASCAL_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                             \
+    } while (0)
+#define RASCAL_LAUNCH_CHECK(what)                                                                       \
+    do {                                                                                                \
+        cudaError_t e_ = cudaGetLastError();                                                            \
+        if (e_ != cudaSuccess)                                                                          \
+            return ::rascal::set_error(RASCAL_E_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e_)); \
+    } while (0)
+
+// -------------------------------------------------------------------------------------------- context
+struct Arena {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Launch plan of the pair/expansion kernels, derived from the hypers once per context.
+//   padded radial index: n in [0, n_pad), n_pad = n_max rounded up to 4
+//   padded angular index: per l a block of mp(l) = 4*ceil((2l+1)/4) slots, slot s <-> m = s - l (s <= 2l valid),
+//   block start lp(l); Lp = sum_l mp(l)
+//   a task is (l, n-tile of 4, m-tile of 4) of one species: T_s tasks per species, W_s warps per species,
+//   S_c species accumulated concurrently, rounds = ceil(n_species / S_c)
+struct ExpPlan {
+    int n_pad, F_pad, Lp;
+    int lp[kMaxLMax + 2];
+    int T_s, W_s, S_c, rounds, threads;
+    int chunk;        // pairs staged per chunk
+    size_t smem;      // dynamic shared memory of the expansion kernel
+    size_t smem_ps;   // extra dynamic shared memory when the power spectrum is fused
+};
+
+}  // namespace rascal
+
+struct rascal_ctx {
+    // hypers (copied)
+    double r_cut, smooth_width, sigma;
+    int n_max, l_max, n_species, radial, orthonormal, include_center, ps_norm;
+    int species[rascal::kMaxSpecies];  // sorted labels
+    cudaStream_t stream;
+    int device;
+    int n_sm;
+
+    // derived
+    int n_lm;        // (l_max+1)^2
+    int F;           // n_max * (l_max+1) radial functions, index f = l*n_max + n
+    int Q;           // n_species * n_max
+
+    // radial table: FP32 cubic coefficients per interval, [M][F] float4 (c0 + u c1 + u^2 c2 + u^3 c3, u in [0,1])
+    float4* d_table;
+    int M;
+    float inv_delta;  // M / r_cut
+    double spline_error, spline_error_fp32;
+
+    // FP64 constants on the device
+    double* d_T;        // [n_max][n_max] S^-1/2 (identity when orthonormal == 0)
+    double* d_gto;      // [3][n_max+1]: d_n, N_n, (unused) for n = 0..n_max
+    double* d_switch;   // [(n_max+1)][(l_max+2)] series/asymptotic switch points of G(a,b)
+    int* d_lut;         // [256] label -> species index or -1
+
+    unsigned* d_flags;  // device error flags (see kFlag*)
+    unsigned* h_flags;  // pinned host mirror
+
+    rascal::Arena scratch;  // grown on demand, reused across calls
+    rascal::Arena scratch2;
+    int64_t* h_pinned;      // pinned host words for small read-backs
+
+    rascal::ExpPlan plan;
+    int* d_tasks;   // [T_s] packed (l, n-tile, m-tile) of the accumulation tasks
+    int* d_fmap;    // [F_pad] table column (l*n_max + n) of a padded radial slot, -1 for padding
+    int* d_pstasks; // power-spectrum tasks, see power_spectrum.cu
+    int n_pstasks;
+};
+
+namespace rascal {
+
+// Returns a device buffer of at least `bytes` from the arena (grows it, never shrinks). Not thread-safe per ctx.
+int arena_get(Arena& a, size_t bytes, void** out);
+// Turns device flags into a status (after the stream has been synchronised), then clears them.
+int check_flags(rascal_ctx* ctx);
+
+// round up
+__host__ __device__ inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+// Carves consecutive, 256-byte aligned sub-buffers out of one scratch allocation.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <typename T>
+    T* take(size_t count) {
+        T* p = reinterpret_cast<T*>(base + off);
+        off = align_up(off + count * sizeof(T), 256);
+        return p;
+    }
+};
+template <typename... Ts>
+inline size_t carve_bytes(Ts... sizes) {
+    size_t s = 0;
+    for (size_t x : {static_cast<size_t>(sizes)...}) s += align_up(x, 256);
+    return s;
+}
+
+// device-wide exclusive scan: out[0..n] with out[n] = total; in and out may alias. Input int32 or int64.
+int scan_exclusive(const int* in, int64_t* out, int64_t n, cudaStream_t stream, Arena& scratch);
+int scan_exclusive(const int64_t* in, int64_t* out, int64_t n, cudaStream_t stream, Arena& scratch);
+
+int validate_system(const rascal_ctx* ctx, const rascal_system* sys);
+
+// per-translation-unit setup called from rascal_create
+int expansion_setup(rascal_ctx* ctx);
+int power_spectrum_setup(rascal_ctx* ctx);
+int gradients_setup(rascal_ctx* ctx);
+
+}  // namespace rascal

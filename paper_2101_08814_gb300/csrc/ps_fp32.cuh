@@ -1,0 +1,68 @@
+// FP32 per-l Gram of the power spectrum (Eq. nu2-basis-coupled in the real basis):
+//   p_{q1 q2 l} = k_l sum_m C[q1][l m] C[q2][l m],   k_l = (2l+1)^-1/2 (or 1 without ps_norm)
+// from one centre's coefficients held transposed in shared memory, CT[lm][q] with q = a n_max + n contiguous and
+// rows padded to Qp (a multiple of 4; columns Q..Qp-1 are zero). A task is a 4 x 4 output tile (l, t1 <= t2);
+// tasks are ordered by decreasing l and dealt round-robin to the CTA's threads.
+#pragma once
+
+#include "common.cuh"
+
+namespace rascal {
+
+__device__ inline int64_t packed_index(int q1, int q2, int Q) {  // q1 <= q2
+    return (int64_t)q1 * Q - (int64_t)q1 * (q1 - 1) / 2 + (q2 - q1);
+}
+
+// tasks: packed (l | t1 << 8 | t2 << 16); out points at this centre's p block
+__device__ inline void ps_gram_fp32(const float* __restrict__ CT, int Qp, int Q, int l_max, int ps_norm,
+                                    const int* __restrict__ tasks, int n_tasks, int layout, float* __restrict__ out) {
+    const int Qpk = Q * (Q + 1) / 2;
+    for (int t = threadIdx.x; t < n_tasks; t += blockDim.x) {
+        const int packed = __ldg(&tasks[t]);
+        const int l = packed & 0xff, t1 = (packed >> 8) & 0xff, t2 = (packed >> 16) & 0xff;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+        const float* row = CT + (size_t)(l * l) * Qp;
+        for (int s = 0; s <= 2 * l; ++s, row += Qp) {
+            const float4 a = *reinterpret_cast<const float4*>(row + 4 * t1);
+            const float4 b = *reinterpret_cast<const float4*>(row + 4 * t2);
+            const float aa[4] = {a.x, a.y, a.z, a.w}, bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(aa[u], bb[v], acc[u][v]);
+        }
+        const float k = ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f;
+        if (layout == RASCAL_LAYOUT_PACKED) {
+            float* o = out + (int64_t)l * Qpk;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q1 = 4 * t1 + u;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int q2 = 4 * t2 + v;
+                    if (q1 <= q2 && q2 < Q) o[packed_index(q1, q2, Q)] = k * acc[u][v];
+                }
+            }
+        } else {
+            float* o = out + (int64_t)l * Q * Q;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q1 = 4 * t1 + u;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int q2 = 4 * t2 + v;
+                    if (q1 < Q && q2 < Q) {
+                        o[(int64_t)q1 * Q + q2] = k * acc[u][v];
+                        if (t1 != t2) o[(int64_t)q2 * Q + q1] = k * acc[u][v];
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace rascal

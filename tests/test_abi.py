@@ -1,0 +1,62 @@
+"""The C-ABI library loads without a GPU and exports every entry point that include/*.h declares."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(rascal_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def library():
+    from paper_2101_08814_gb300 import build
+
+    try:
+        path = build.build()
+    except RuntimeError as e:  # no nvcc on this machine
+        pytest.skip(str(e))
+    return path
+
+
+def test_every_declared_symbol_is_exported(library):
+    import ctypes
+
+    names = _declared()
+    assert "rascal_neighbours" in names and "rascal_power_spectrum" in names
+    handle = ctypes.CDLL(library)
+    missing = [n for n in sorted(names) if not hasattr(handle, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", library], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (rascal_\w+)", out))
+    assert names <= exported
+
+
+def test_binding_declares_only_header_symbols(library):
+    from paper_2101_08814_gb300 import _lib
+
+    assert set(_lib.exported_symbols()) <= _declared()
+    _lib.lib()  # loads and binds every signature without touching the GPU
+
+
+def test_error_path_without_device(library):
+    # a NULL hypers pointer is rejected before any CUDA call
+    import ctypes
+
+    from paper_2101_08814_gb300 import _lib
+
+    out = ctypes.c_void_p()
+    st = _lib.lib().rascal_create(None, None, ctypes.byref(out))
+    assert st == _lib.RASCAL_E_ARG
+    assert b"NULL" in _lib.lib().rascal_last_error()

@@ -1,0 +1,136 @@
+"""GPU radial table, spherical expansion and FP32 power spectrum against the FP64 oracle.
+
+Tolerance (FP32 path): per (centre, species) block of c and per (centre, l) block of p,
+max |gpu - oracle| / max |oracle| <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import radial as oradial  # noqa: E402
+from oracle import soap as osoap  # noqa: E402
+from synth import System, config_batch, config_tiny, random_cell_atoms, small_cell_system  # noqa: E402
+from tests.gpu_common import block_rel_err, ps_blocks  # noqa: E402
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rg():
+    import paper_2101_08814_gb300 as rg
+
+    return rg
+
+
+def _run(rg, system, layout="packed", **over):
+    h = dict(system.hypers, **over)
+    calc = rg.SoapCalculator(**h)
+    ds = rg.DeviceSystem.from_numpy(system)
+    pairs = calc.neighbours(ds)
+    c = calc.spherical_expansion(ds, pairs)
+    p = calc.power_spectrum(c, layout=layout)
+    calc.sync()
+    return calc, c.cpu().numpy(), p.cpu().numpy()
+
+
+def test_radial_exact_fp64_matches_oracle(rg):
+    import torch
+
+    for hyp in (dict(r_cut=5.0, sigma=0.5, n_max=8, l_max=6), dict(r_cut=6.0, sigma=0.5, n_max=16, l_max=12),
+                dict(r_cut=5.5, sigma=0.4, n_max=8, l_max=6)):
+        calc = rg.SoapCalculator(**hyp, species=[1])
+        r = np.linspace(0.0, hyp["r_cut"], 97)
+        I, dI = calc.radial_exact_fp64(torch.tensor(r), derivative=True)
+        Ir, dIr = oradial.integrals(r, hyp["r_cut"], hyp["sigma"], hyp["n_max"], hyp["l_max"], derivative=True)
+        # the o-GTO transform amplifies FP64 rounding by up to cond(S)^1/2 (about 2e5 at n_max = 16)
+        tol = 1e-12 if hyp["n_max"] <= 8 else 5e-10
+        assert np.max(np.abs(I.cpu().numpy() - Ir)) <= tol * np.max(np.abs(Ir))
+        assert np.max(np.abs(dI.cpu().numpy() - dIr)) <= tol * np.max(np.abs(dIr))
+
+
+def test_spline_meets_its_accuracy_target(rg):
+    calc = rg.SoapCalculator(**config_tiny().hypers)
+    assert calc.info["spline_error"] <= 1e-8
+    assert calc.info["spline_error_fp32"] <= 2e-6
+    assert calc.info["spline_intervals"] >= 64
+
+
+def test_tiny_all_centres(rg):
+    s = config_tiny()
+    h = osoap.Hypers(**s.hypers)
+    _, c, p = _run(rg, s)
+    c_ref = osoap.spherical_expansion(s, h)
+    p_ref = osoap.power_spectrum(c_ref, h, "packed")
+    assert block_rel_err(c, c_ref, 2) <= TOL
+    assert block_rel_err(ps_blocks(p, h.l_max), p_ref, 2) <= TOL
+
+
+def test_full_layout_and_raw_basis(rg):
+    s = config_tiny()
+    h = osoap.Hypers(**dict(s.hypers, orthonormal=False))
+    _, c, p = _run(rg, s, layout="full", orthonormal=False)
+    centres = [0, 5, 40]
+    c_ref = osoap.spherical_expansion(s, h, centres=centres)
+    p_ref = osoap.power_spectrum(c_ref, h, "full")
+    assert block_rel_err(c[centres], c_ref, 2) <= TOL
+    assert block_rel_err(ps_blocks(p[centres], h.l_max), p_ref, 2) <= TOL
+
+
+def test_small_cell_self_images_two_species(rg):
+    s = small_cell_system(seed=21, n_atoms=9, L=5.0, hypers=dict(r_cut=5.0, sigma=0.45, n_max=6, l_max=5, smooth_width=0.7,
+                                                                 species=[1, 8]))
+    h = osoap.Hypers(**s.hypers)
+    _, c, p = _run(rg, s)
+    c_ref = osoap.spherical_expansion(s, h)
+    assert block_rel_err(c, c_ref, 2) <= TOL
+    assert block_rel_err(ps_blocks(p, h.l_max), osoap.power_spectrum(c_ref, h, "packed"), 2) <= TOL
+
+
+def test_include_center(rg):
+    s = config_tiny()
+    h = osoap.Hypers(**dict(s.hypers, include_center=True))
+    _, c, _ = _run(rg, s, include_center=True)
+    c_ref = osoap.spherical_expansion(s, h, centres=[3, 7])
+    assert block_rel_err(c[[3, 7]], c_ref, 2) <= TOL
+
+
+def test_many_species_several_rounds(rg):
+    # 8 species with n_max = 16, l_max = 12: the kernel accumulates the species in several rounds
+    rng = np.random.Generator(np.random.PCG64(77))
+    L = 15.0
+    pos = random_cell_atoms(200, np.eye(3) * L, 1.6, rng)
+    labels = [1, 5, 6, 7, 8, 9, 15, 16]
+    s = System(pos, np.asarray(labels, np.int32)[rng.integers(0, 8, 200)], (np.eye(3) * L)[None], np.ones((1, 3), np.int32),
+               np.array([0, 200], np.int32), dict(r_cut=6.0, sigma=0.5, n_max=16, l_max=12, smooth_width=0.5, species=labels))
+    h = osoap.Hypers(**s.hypers)
+    _, c, p = _run(rg, s)
+    centres = [0, 99, 199]
+    c_ref = osoap.spherical_expansion(s, h, centres=centres)
+    # n_max = 16: S^-1/2 carries FP64 rounding amplified by cond(S)^1/2 on both sides, hence 2e-5
+    assert block_rel_err(c[centres], c_ref, 2) <= 2e-5
+    assert block_rel_err(ps_blocks(p[centres], h.l_max), osoap.power_spectrum(c_ref, h, "packed"), 2) <= 2e-5
+
+
+def test_batch_full_size_sampled(rg):
+    s = config_batch()
+    h = osoap.Hypers(**s.hypers)
+    calc, c, p = _run(rg, s)
+    rng = np.random.default_rng(1)
+    centres = np.concatenate([[0, s.n_atoms - 1], rng.choice(s.n_atoms, 14, replace=False)])
+    c_ref = osoap.spherical_expansion(s, h, centres=centres)
+    assert block_rel_err(c[centres], c_ref, 2) <= TOL
+    assert block_rel_err(ps_blocks(p[centres], h.l_max), osoap.power_spectrum(c_ref, h, "packed"), 2) <= TOL
+    assert np.all(np.isfinite(c)) and np.all(np.isfinite(p))
+
+
+def test_fused_soap_equals_separate_calls(rg):
+    s = config_tiny()
+    calc = rg.SoapCalculator(**s.hypers)
+    ds = rg.DeviceSystem.from_numpy(s)
+    pairs = calc.neighbours(ds)
+    c1 = calc.spherical_expansion(ds, pairs)
+    p1 = calc.power_spectrum(c1)
+    c2, p2 = calc.soap(ds, pairs)
+    assert np.array_equal(c1.cpu().numpy(), c2.cpu().numpy())
+    assert np.max(np.abs(p1.cpu().numpy() - p2.cpu().numpy())) <= 1e-6 * np.max(np.abs(p1.cpu().numpy()))
