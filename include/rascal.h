@@ -103,6 +103,9 @@ typedef struct {
 /* Thread-local message of the last failed call on this thread ("" if none). Never NULL. */
 const char* rascal_last_error(void);
 
+/* Diagnostics: number of CUDA kernels this library has launched in the process so far (all contexts). */
+long long rascal_launch_count(void);
+
 /* Build a context: validates the hypers, computes the GTO constants and the FP64 overlap matrix with its
  * inverse square root (Sec. 'GTO radial basis'), tabulates the o-GTO radial integrals in FP64 on the GPU with
  * the series/asymptotic 1F1 of Appendix A, solves the clamped cubic spline and stores FP32 per-interval

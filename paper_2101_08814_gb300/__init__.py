@@ -18,6 +18,11 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
 
 
+def launch_count() -> int:
+    """Kernels the library has launched in this process (all contexts)."""
+    return int(_lib.lib().rascal_launch_count())
+
+
 @dataclass
 class DeviceSystem:
     """Structures resident on the GPU (tensors kept alive for the duration of the calls)."""

@@ -76,6 +76,7 @@ _lib = None
 # name -> (restype, argtypes)
 _SIGNATURES = {
     "rascal_last_error": (C.c_char_p, []),
+    "rascal_launch_count": (C.c_longlong, []),
     "rascal_create": (C.c_int, [C.POINTER(Hypers), C.c_void_p, C.POINTER(C.c_void_p)]),
     "rascal_destroy": (None, [C.c_void_p]),
     "rascal_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),

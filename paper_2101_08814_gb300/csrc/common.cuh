@@ -39,8 +39,12 @@ void clear_error();
             return ::rascal::set_error(RASCAL_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
                                        __FILE__, __LINE__);                                             \
     } while (0)
+// Every kernel launch is followed by exactly one RASCAL_LAUNCH_CHECK: it counts the launch (see
+// rascal_launch_count) and turns a launch error into RASCAL_E_CUDA.
+void count_launch();
 #define RASCAL_LAUNCH_CHECK(what)                                                                       \
     do {                                                                                                \
+        ::rascal::count_launch();                                                                       \
         cudaError_t e_ = cudaGetLastError();                                                            \
         if (e_ != cudaSuccess)                                                                          \
             return ::rascal::set_error(RASCAL_E_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e_)); \

@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -13,6 +14,9 @@
 namespace rascal {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int set_error(int code, const char* fmt, ...) {
     char buf[1024];
@@ -319,7 +323,9 @@ static int build_table(rascal_ctx* ctx, int M, double* errs_host) {
     double* y2 = cv.take<double>((size_t)F * (M + 1));
     double* err = cv.take<double>(2);
     k_fill_grid<<<div_up(M + 1, 256), 256, 0, ctx->stream>>>(M + 1, delta, 0.0, grid);
+    RASCAL_LAUNCH_CHECK("k_fill_grid");
     k_fill_grid<<<div_up(M, 256), 256, 0, ctx->stream>>>(M, delta, 0.5 * delta, mids);
+    RASCAL_LAUNCH_CHECK("k_fill_grid");
     k_fill_grid<<<1, 32, 0, ctx->stream>>>(2, ctx->r_cut, 0.0, ends);
     RASCAL_LAUNCH_CHECK("k_fill_grid");
     if ((st = launch_radial_fp64(ctx, M + 1, grid, y, nullptr))) return st;
@@ -348,6 +354,8 @@ static int build_table(rascal_ctx* ctx, int M, double* errs_host) {
 using namespace rascal;
 
 extern "C" const char* rascal_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" long long rascal_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 extern "C" void rascal_destroy(rascal_ctx* ctx) {
     if (!ctx) return;

@@ -491,8 +491,9 @@ extern "C" int rascal_neighbours(rascal_ctx* ctx, const rascal_system* sys, int6
     RASCAL_LAUNCH_CHECK("k_atom_bin");
     if ((st = scan_exclusive(bin_count, bin_start, nbins_cap, stream, ctx->scratch2))) return st;
     k_atom_scatter<<<(unsigned)div_up(N, 256), 256, 0, stream>>>(N, atom_bin, atom_rank, bin_start, atom_hi, sorted_hi);
-    k_struct_thresholds<<<(unsigned)div_up(n_s, 128), 128, 0, stream>>>(n_s, ctx->r_cut, info);
     RASCAL_LAUNCH_CHECK("k_atom_scatter");
+    k_struct_thresholds<<<(unsigned)div_up(n_s, 128), 128, 0, stream>>>(n_s, ctx->r_cut, info);
+    RASCAL_LAUNCH_CHECK("k_struct_thresholds");
     const double rc2 = ctx->r_cut * ctx->r_cut;
     const unsigned pair_blocks = (unsigned)div_up(N, kPairWarps);
     k_pairs<false><<<pair_blocks, kPairWarps * 32, 0, stream>>>(N, sys->d_positions, info, binbase, bin_start, sorted_hi,

@@ -87,9 +87,13 @@ static int scan_impl(const Tin* in, int64_t* out, int64_t n, cudaStream_t stream
     if (st) return st;
     int64_t* sums = static_cast<int64_t*>(buf);
     k_scan_tiles<Tin><<<(unsigned)tiles, kScanThreads, 0, stream>>>(in, out, n, sums);
+    RASCAL_LAUNCH_CHECK("k_scan_tiles");
     k_scan_tile_sums<<<1, kScanThreads, 0, stream>>>(sums, tiles, out + n);
-    if (tiles > 1) k_scan_add<<<(unsigned)tiles, kScanThreads, 0, stream>>>(out, n, sums);
-    RASCAL_LAUNCH_CHECK("scan");
+    RASCAL_LAUNCH_CHECK("k_scan_tile_sums");
+    if (tiles > 1) {
+        k_scan_add<<<(unsigned)tiles, kScanThreads, 0, stream>>>(out, n, sums);
+        RASCAL_LAUNCH_CHECK("k_scan_add");
+    }
     return RASCAL_OK;
 }
 

@@ -40,6 +40,30 @@ def test_ogto_basis_is_orthonormal():
     assert np.allclose(T @ S @ T, np.eye(NMAX), atol=1e-9)
 
 
+def test_inverse_sqrt_accuracy_against_40_digits():
+    # S^-1/2 is ill-conditioned (cond S = 5.7e10 at r_cut 6, n_max 16); the FP64 result must be within
+    # eps cond(S) of a 40-digit computation of the same closed form
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    rc, n = 6.0, 16
+    Sm = mpmath.matrix(n, n)
+    for i in range(n):
+        for j in range(n):
+            si = mpmath.mpf(rc) * max(mpmath.sqrt(i), 1) / n
+            sj = mpmath.mpf(rc) * max(mpmath.sqrt(j), 1) / n
+            di, dj = 1 / (2 * si ** 2), 1 / (2 * sj ** 2)
+            Ni = mpmath.sqrt(2 / (si ** (2 * i + 3) * mpmath.gamma(i + mpmath.mpf(3) / 2)))
+            Nj = mpmath.sqrt(2 / (sj ** (2 * j + 3) * mpmath.gamma(j + mpmath.mpf(3) / 2)))
+            p = mpmath.mpf(i + j + 3) / 2
+            Sm[i, j] = Ni * Nj * mpmath.gamma(p) / 2 * (di + dj) ** (-p)
+    E, V = mpmath.eigsy(Sm)
+    T = np.array((V * mpmath.diag([1 / mpmath.sqrt(e) for e in E]) * V.T).tolist(), dtype=float)
+    S = gto.gto_overlap(rc, n)
+    assert np.allclose(S, np.array(Sm.tolist(), dtype=float), rtol=1e-14, atol=1e-15)
+    err = np.max(np.abs(gto.orthonormalisation(rc, n) - T)) / np.max(np.abs(T))
+    assert err < 2.2e-16 * np.linalg.cond(S)
+
+
 @pytest.mark.parametrize("r", [0.0, 0.3, 1.1, 2.5, 3.7, 4.99])
 def test_closed_form_matches_quadrature(r):
     # Eq. rad-int-gto-1 against Eq. radial-integral-gaussian-density by quadrature (scipy Bessel)
