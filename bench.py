@@ -54,15 +54,16 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--structures", type=int, default=512, help="cells in the batch workload (profiling cases)")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
 
-def make_system(config: str, rank: int):
+def make_system(config: str, rank: int, n_structures: int = 512):
     from synth import structures
 
     if config == "batch":
-        return structures.config_batch(seed=2 + 1000 * rank)
+        return structures.config_batch(seed=2 + 1000 * rank, n_structures=n_structures)
     fn = {"tiny": structures.config_tiny, "diff": structures.config_diff, "large": structures.config_large,
           "mlp": structures.config_mlp}[config]
     default_seed = {"tiny": 1, "diff": 3, "large": 5, "mlp": 6}[config]
@@ -236,7 +237,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     import paper_2101_08814_gb300 as rg
 
-    system = make_system(args.config, rank)
+    system = make_system(args.config, rank, args.structures)
     calc = rg.SoapCalculator(**system.hypers, device=dev)
     ds = rg.DeviceSystem.from_numpy(system, device=dev)
     N = ds.n_atoms
