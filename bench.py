@@ -49,8 +49,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="batch")
     ap.add_argument("--layout", choices=["packed", "full"], default="packed")
-    ap.add_argument("--ps", choices=["fp32", "bf16"], default="fp32")
-    ap.add_argument("--fused", action="store_true", help="one rascal_soap call instead of expansion + power spectrum")
+    ap.add_argument("--ps", choices=["fp32", "bf16", "tf32x3"], default="fp32")
+    ap.add_argument("--separate", action="store_true",
+                    help="rascal_spherical_expansion + rascal_power_spectrum instead of the fused rascal_soap")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -254,13 +255,13 @@ def run_ours(args):
         pairs = calc.neighbours(ds)
         if events is not None:
             events[1].record(stream)
-        if not args.fused or args.ps != "fp32":
+        if args.separate:
             calc.spherical_expansion(ds, pairs, out=coeffs)
             if events is not None:
                 events[2].record(stream)
             calc.power_spectrum(coeffs, precision=args.ps, layout=args.layout, out=ps)
         else:
-            calc.soap(ds, pairs, layout=args.layout, coeffs=coeffs, ps=ps)
+            calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps)
             if events is not None:
                 events[2].record(stream)
         if events is not None:
@@ -304,9 +305,9 @@ def run_ours(args):
     pair_in = 24 * n_pairs + 8 * (N + 1)                      # r_ji float4 + j + species(j); CSR offsets
     c_bytes = 4 * Qc * N
     p_bytes = 4 * Fp * N
-    fused = not (not args.fused or args.ps != "fp32")
+    fused = not args.separate
     if fused:
-        kernel, alg, t_ms = "rascal_soap (expansion + power spectrum)", pair_in + c_bytes + p_bytes, mean[1]
+        kernel, alg, t_ms = "k_expansion<fused power spectrum> (rascal_soap)", pair_in + c_bytes + p_bytes, mean[1]
         if mean[0] > mean[1]:
             kernel, alg, t_ms = "rascal_neighbours", None, mean[0]
     else:
@@ -377,7 +378,7 @@ def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None):
         for k in host:
             dev_t[k].copy_(host[k], non_blocking=True)
         pairs = calc.neighbours(ds)
-        calc.soap(ds, pairs, layout=args.layout, coeffs=coeffs, ps=ps)
+        calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps)
         out_host.copy_(ps, non_blocking=True)
 
     for _ in range(2):

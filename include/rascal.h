@@ -42,6 +42,7 @@ extern "C" {
 #define RASCAL_E_CUDA (-3)        /* a CUDA runtime call failed */
 #define RASCAL_E_UNSUPPORTED (-4) /* valid input outside what the kernels support (e.g. |shift| > 511) */
 #define RASCAL_E_GEOMETRY (-5)    /* degenerate geometry: singular cell, coincident atoms (r < 1e-6 A) */
+#define RASCAL_E_TIMEOUT (-6)     /* a bounded device-side wait ran out (reported by rascal_sync / the next check) */
 #define RASCAL_E_NOMEM (-7)       /* device allocation of context scratch failed */
 
 /* radial integral source */
@@ -50,8 +51,10 @@ extern "C" {
 #define RASCAL_RADIAL_MLP 2    /* the trained MLP surrogate held by the context */
 
 /* power-spectrum arithmetic */
-#define RASCAL_PS_FP32 0 /* FP32 inputs and accumulation (CUDA cores) */
-#define RASCAL_PS_BF16 1 /* BF16 inputs, FP32 accumulation (tcgen05 tensor cores) */
+#define RASCAL_PS_FP32 0   /* FP32 inputs and accumulation (CUDA cores) */
+#define RASCAL_PS_BF16 1   /* BF16 inputs, FP32 accumulation (tcgen05 tensor cores) */
+#define RASCAL_PS_TF32X3 2 /* FP32 inputs split into TF32 hi + lo, three tcgen05 MMAs, FP32 accumulation:
+                              about 2^-21 relative per product, FP32-grade results on tensor cores */
 
 /* power-spectrum layout */
 #define RASCAL_LAYOUT_PACKED 0
@@ -143,9 +146,11 @@ int rascal_spherical_expansion(rascal_ctx* ctx, const rascal_system* sys, const 
 int rascal_power_spectrum(rascal_ctx* ctx, int64_t n_centres, const float* d_coeffs, int precision, int layout,
                           float* d_ps);
 
-/* Expansion and power spectrum in one pass: c is written to d_coeffs and p to d_ps (FP32 arithmetic). */
+/* Expansion and power spectrum in one kernel: each centre's c is written to d_coeffs and kept in shared memory,
+ * where its Gram is formed (precision as in rascal_power_spectrum; RASCAL_PS_FP32 uses the CUDA cores, the
+ * others tcgen05), so c is never read back from global memory. */
 int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,
-                const float* d_rij, int layout, float* d_coeffs, float* d_ps);
+                const float* d_rij, int precision, int layout, float* d_coeffs, float* d_ps);
 
 /* Per-structure energy of the additive linear model E = sum_i w_{a_i} . p_i (Eq. additive-energy-model) from
  * PACKED p: d_weights [n_species][features_packed] float32, d_energy [n_structures] float64 (overwritten). */

@@ -166,7 +166,8 @@ class SoapCalculator:
                                                     _ptr(p)))
         return p
 
-    def soap(self, system: DeviceSystem, pairs: PairList, layout="packed", coeffs=None, ps=None):
+    def soap(self, system: DeviceSystem, pairs: PairList, layout="packed", precision="fp32", coeffs=None, ps=None):
+        """Expansion and power spectrum in one fused kernel launch."""
         import torch
 
         self._bind_stream()
@@ -176,7 +177,7 @@ class SoapCalculator:
         p = ps if ps is not None else torch.empty((N, self.n_features(layout)), dtype=torch.float32, device=self.device)
         sys_c = system.c_struct()
         _lib.check(_lib.lib().rascal_soap(self._ctx, C.byref(sys_c), _ptr(pairs.offsets), _ptr(pairs.nbr_j),
-                                          _ptr(pairs.rij), LAYOUT[layout], _ptr(c), _ptr(p)))
+                                          _ptr(pairs.rij), PRECISION[precision], LAYOUT[layout], _ptr(c), _ptr(p)))
         return c, p
 
     def linear_energy(self, system: DeviceSystem, ps_packed, weights):

@@ -13,10 +13,11 @@ RASCAL_E_CAPACITY = -2
 RASCAL_E_CUDA = -3
 RASCAL_E_UNSUPPORTED = -4
 RASCAL_E_GEOMETRY = -5
+RASCAL_E_TIMEOUT = -6
 RASCAL_E_NOMEM = -7
 
 RADIAL = {"spline": 0, "exact": 1, "mlp": 2}
-PRECISION = {"fp32": 0, "bf16": 1}
+PRECISION = {"fp32": 0, "bf16": 1, "tf32x3": 2}
 LAYOUT = {"packed": 0, "full": 1}
 
 
@@ -87,7 +88,7 @@ _SIGNATURES = {
     "rascal_spherical_expansion": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p]),
     "rascal_power_spectrum": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
-    "rascal_soap": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+    "rascal_soap": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                               C.c_void_p, C.c_void_p]),
     "rascal_linear_energy": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p]),
     "rascal_gradients": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,

@@ -27,6 +27,7 @@ enum : unsigned {
     kFlagThinCell = 1u << 2,    // perpendicular cell width below r_cut / 64
     kFlagShiftRange = 1u << 3,  // |n_k| above kMaxShift
     kFlagBadOffsets = 1u << 4,  // structure offsets not increasing / out of range
+    kFlagTimeout = 1u << 5,     // a bounded wait on a tensor-core completion barrier ran out
 };
 
 // -------------------------------------------------------------------------------------------- status

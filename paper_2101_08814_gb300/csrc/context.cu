@@ -60,6 +60,7 @@ int check_flags(rascal_ctx* ctx) {
     if (f & kFlagGeometry) return set_error(RASCAL_E_GEOMETRY, "singular cell or coincident atoms (r < 1e-6 A)");
     if (f & kFlagThinCell) return set_error(RASCAL_E_UNSUPPORTED, "a cell is thinner than r_cut/64 along some axis");
     if (f & kFlagShiftRange) return set_error(RASCAL_E_UNSUPPORTED, "a periodic shift exceeds |n| <= 511");
+    if (f & kFlagTimeout) return set_error(RASCAL_E_TIMEOUT, "a bounded wait for tensor-core completion timed out");
     return set_error(RASCAL_E_CUDA, "unknown device flag 0x%x", f);
 }
 

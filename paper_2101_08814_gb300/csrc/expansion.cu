@@ -1,5 +1,7 @@
-// Fused pair kernel for the density coefficients (Eq. spherical_expansion_coefficients_gaussians):
+// Fused pair kernel for the density coefficients (Eq. spherical_expansion_coefficients_gaussians), optionally
+// followed in the same CTA by the power spectrum (Eq. nu2-basis-coupled):
 //   c^i_{a n l m} = sum_{j in A_i, a_j = a} f_cut(r_ji) I^o_nl(r_ji) Y_lm(r^_ji)
+//   p^i_{q1 q2 l} = (2l+1)^-1/2 sum_m c^i_{q1 l m} c^i_{q2 l m}
 //
 // One CTA per centre i. The centre's CSR segment of pairs is processed in chunks staged in shared memory:
 //   1. stage r_ji (float4 x, y, z, r), the neighbour's species and f_cut(r) for the chunk;
@@ -8,15 +10,29 @@
 //      G_nl = f_cut(r) I^o_nl(r) from the FP32 cubic spline table (one warp per pair, lanes over (l, n));
 //   4. accumulate: each thread owns a 4(n) x 4(m) register tile of one l and one species and adds the outer
 //      product G_{l, n-tile} x Y_{l, m-tile} for every pair of its species (16 FMAs per two float4 loads).
-// The segment reduction happens in registers; no atomics, no intermediate written to global memory.
-// Output stores go to the centre's contiguous block [n_species][n_max][(l_max+1)^2].
+// The segment reduction happens in registers; no atomics. The tiles are stored to the centre's block of c in global
+// memory and, when the power spectrum is fused, also into shared memory, where the Gram runs without c ever being
+// read back from HBM:
+//   kGramSimt    FP32 register-tiled Gram on the CUDA cores from CT[lm][q] (ps_fp32.cuh);
+//   kGramBf16    tcgen05 MMA, BF16 operands, FP32 accumulators in TMEM (tcgen05.cuh);
+//   kGramTf32x3  tcgen05 MMA, TF32 hi/lo split, three MMAs per K step (FP32-grade).
+// The Gram output is staged per group of l values in the (then free) pair-staging buffers and written to global
+// memory with coalesced stores.
+#include <cuda_bf16.h>
+
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
+#include "ps_fp32.cuh"
+#include "tcgen05.cuh"
 #include "ylm_fp32.cuh"
 
 namespace rascal {
+
+enum GramMode : int { kGramNone = 0, kGramSimt = 1, kGramBf16 = 2, kGramTf32x3 = 3 };
+constexpr int kMaxGroups = kMaxLMax + 2;
 
 struct ExpArgs {
     const int64_t* offsets;
@@ -32,6 +48,19 @@ struct ExpArgs {
     int N, n_max, l_max, S, n_lm, F, F_pad, n_pad, Lp, M, T_s, W_s, S_c, rounds, chunk, include_center;
     float inv_delta, r_cut, width;
     int lp[kMaxLMax + 2];
+    // fused power spectrum
+    float* ps;
+    int64_t ps_stride;
+    int layout, ps_norm, Q, per_l;
+    int gram_off;                   // bytes: CT (SIMT) or operand tiles (tensor cores)
+    int stage_floats;               // capacity of the staging area (aliases the pair buffers)
+    int n_groups;
+    int g_lo[kMaxGroups], g_hi[kMaxGroups];      // l range [g_lo, g_hi) of each output group
+    const int* ps_tasks;            // SIMT tasks, l descending
+    int g_tbeg[kMaxGroups], g_tend[kMaxGroups];  // SIMT task ranges of the groups
+    int Qp;                         // SIMT CT row pitch
+    int N_mma, tm_cols, lo_off, tiles_bytes;
+    int tile_off[kMaxLMax + 1], sbo[kMaxLMax + 1], nk[kMaxLMax + 1];
 };
 
 __device__ inline float cutoff_fp32(float r, float r_cut, float w) {
@@ -40,17 +69,12 @@ __device__ inline float cutoff_fp32(float r, float r_cut, float w) {
     return 0.5f * (1.0f + cospif((r - r_cut + w) / w));
 }
 
-__device__ inline float spline_eval(const float4* __restrict__ table, int F, int M, float inv_delta, float r, int col) {
-    const float x = r * inv_delta;
-    int k = (int)x;
-    k = min(max(k, 0), M - 1);
-    const float u = x - (float)k;
-    const float4 c = __ldg(&table[(int64_t)k * F + col]);
-    return fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
-}
-
-__global__ void __launch_bounds__(1024) k_expansion(const ExpArgs A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+template <int GRAM>
+__global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    constexpr bool TC = (GRAM == kGramBf16 || GRAM == kGramTf32x3);
     const int chunk = A.chunk;
     float4* s_vec = reinterpret_cast<float4*>(smem_raw);
     float* s_G = reinterpret_cast<float*>(s_vec + chunk);            // [chunk][F_pad]
@@ -61,11 +85,31 @@ __global__ void __launch_bounds__(1024) k_expansion(const ExpArgs A) {
     int* s_start = s_list + chunk;                                    // [kMaxSpecies + 1]
     int* s_lp = s_start + (kMaxSpecies + 1);                          // [kMaxLMax + 2]
     int* s_fmap = s_lp + (kMaxLMax + 2);                              // [F_pad]
+    unsigned char* gram = smem_raw + A.gram_off;                      // CT or tiles
+    float* stage = s_G;                                               // reused once the pairs are done
 
     const int i = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     if (tid < kMaxLMax + 2) s_lp[tid] = A.lp[tid];
     for (int t = tid; t < A.F_pad; t += blockDim.x) s_fmap[t] = A.fmap[t];
+    if (GRAM == kGramSimt) {  // padding columns Q..Qp-1 of CT must read as zero
+        float* CT = reinterpret_cast<float*>(gram);
+        const int padc = A.Qp - A.Q;
+        for (int e = tid; e < A.n_lm * padc; e += blockDim.x) CT[(e / padc) * A.Qp + A.Q + e % padc] = 0.0f;
+    }
+    if (TC) {  // K padding and rows >= Q of the operand tiles must read as zero
+        for (int b = tid; b < A.tiles_bytes / 16; b += blockDim.x)
+            reinterpret_cast<uint4*>(gram)[b] = make_uint4(0, 0, 0, 0);
+        if (warp == 0) {
+            tmem_alloc(&s_tmem, (uint32_t)A.tm_cols);
+            tmem_relinquish();
+        }
+        if (tid == 0) {
+            mbar_init(&s_bar, 1);
+            fence_mbar_init();
+        }
+        tc_fence_before();
+    }
     const int64_t seg_beg = A.offsets[i], seg_end = A.offsets[i + 1];
     const int L1 = A.l_max + 1;
 
@@ -168,6 +212,7 @@ __global__ void __launch_bounds__(1024) k_expansion(const ExpArgs A) {
                 const float u = x - (float)k;
                 const float4* trow = A.table + (int64_t)k * A.F;
                 float* grow = s_G + (size_t)q * A.F_pad;
+#pragma unroll 4
                 for (int fp = lane; fp < A.F_pad; fp += 32) {
                     const int col = s_fmap[fp];
                     float val = 0.0f;
@@ -213,12 +258,132 @@ __global__ void __launch_bounds__(1024) k_expansion(const ExpArgs A) {
             for (int u = 0; u < 4; ++u) {
                 const int n = 4 * my_nt + u;
                 if (n >= A.n_max) continue;
+                const int q = a * A.n_max + n;
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     const int s = 4 * my_mt + v;
-                    if (s <= 2 * my_l) out[(int64_t)n * A.n_lm + s] = acc[u][v];
+                    if (s > 2 * my_l) continue;
+                    const float cv = acc[u][v];
+                    out[(int64_t)n * A.n_lm + s] = cv;
+                    if (GRAM == kGramSimt) {
+                        reinterpret_cast<float*>(gram)[(my_l * my_l + s) * A.Qp + q] = cv;
+                    } else if (TC) {
+                        constexpr int esz = (GRAM == kGramTf32x3) ? 4 : 2, e16 = 16 / esz;
+                        const int off = A.tile_off[my_l] + (q >> 3) * A.sbo[my_l] + (s / e16) * 128 + (q & 7) * 16 + (s % e16) * esz;
+                        if (GRAM == kGramTf32x3) {
+                            const float hi = __uint_as_float(__float_as_uint(cv) & 0xFFFFE000u);
+                            *reinterpret_cast<float*>(gram + off) = hi;
+                            *reinterpret_cast<float*>(gram + A.lo_off + off) = cv - hi;
+                        } else {
+                            *reinterpret_cast<__nv_bfloat16*>(gram + off) = __float2bfloat16_rn(cv);
+                        }
+                    }
                 }
             }
+        }
+    }
+    if (GRAM == kGramNone) return;
+
+    // ------------------------------------------------------------------------------------ fused power spectrum
+    float* pout = A.ps + (int64_t)i * A.ps_stride;
+    if (GRAM == kGramSimt) {
+        __syncthreads();
+        const float* CT = reinterpret_cast<const float*>(gram);
+        for (int gi = 0; gi < A.n_groups; ++gi) {
+            const int lo = A.g_lo[gi];
+            for (int t = A.g_tbeg[gi] + tid; t < A.g_tend[gi]; t += blockDim.x) {
+                const int packed = __ldg(&A.ps_tasks[t]);
+                const int l = packed & 0xff, t1 = (packed >> 8) & 0xff, t2 = (packed >> 16) & 0xff;
+                float acc[4][4];
+                gram_tile_fp32(CT, A.Qp, l, t1, t2, acc);
+                store_tile_fp32(stage + (size_t)(l - lo) * A.per_l, A.Q, A.layout, t1, t2,
+                                A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f, acc);
+            }
+            __syncthreads();
+            float* dst = pout + (int64_t)lo * A.per_l;
+            const int count = (A.g_hi[gi] - lo) * A.per_l;
+            for (int t = tid; t < count; t += blockDim.x) dst[t] = stage[t];
+            __syncthreads();
+        }
+        return;
+    }
+    if (TC) {
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const uint32_t taddr = s_tmem;
+        const uint32_t tiles_s = smem_u32(gram);
+        const uint32_t idesc = instr_desc(GRAM == kGramTf32x3 ? 2u : 1u, 128u, (uint32_t)A.N_mma);
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int gi = 0; gi < A.n_groups && ok; ++gi) {
+            const int l0 = A.g_lo[gi], l1 = A.g_hi[gi];
+            if (tid == 0) {
+                tc_fence_after();
+                for (int l = l0; l < l1; ++l) {
+                    const uint32_t d = taddr + (uint32_t)((l - l0) * A.N_mma);
+                    for (int kk = 0; kk < A.nk[l]; ++kk) {
+                        const uint32_t a_addr = tiles_s + A.tile_off[l] + kk * 256;
+                        const uint64_t da = smem_desc(a_addr, 128, A.sbo[l]);
+                        if (GRAM == kGramTf32x3) {
+                            const uint64_t dl = smem_desc(a_addr + A.lo_off, 128, A.sbo[l]);
+                            mma_tf32_ss(d, da, da, idesc, kk > 0);
+                            mma_tf32_ss(d, da, dl, idesc, 1);
+                            mma_tf32_ss(d, dl, da, idesc, 1);
+                        } else {
+                            mma_bf16_ss(d, da, da, idesc, kk > 0);
+                        }
+                    }
+                }
+                mma_commit(&s_bar);
+            }
+            const bool done = mbar_wait_bounded(&s_bar, phase);
+            ok = __syncthreads_and(done) != 0;
+            if (!ok) {
+                if (tid == 0) atomicOr(A.flags, kFlagTimeout);
+                mbar_wait_bounded(&s_bar, phase);
+            }
+            phase ^= 1u;
+            tc_fence_after();
+            if (ok && warp < 4) {
+                const int q = 32 * warp + lane;
+                for (int l = l0; l < l1; ++l) {
+                    const float kl = A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f;
+                    float* st = stage + (size_t)(l - l0) * A.per_l;
+                    for (int jb = 0; jb < A.N_mma / 16; ++jb) {
+                        float v[16];
+                        tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)((l - l0) * A.N_mma + 16 * jb), v);
+                        if (q < A.Q) {
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) {
+                                const int q2 = 16 * jb + t;
+                                if (q2 < A.Q) {
+                                    if (A.layout == RASCAL_LAYOUT_PACKED) {
+                                        if (q2 >= q) st[packed_index(q, q2, A.Q)] = kl * v[t];
+                                    } else {
+                                        st[q * A.Q + q2] = kl * v[t];
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            if (ok) {
+                float* dst = pout + (int64_t)l0 * A.per_l;
+                const int count = (l1 - l0) * A.per_l;
+                for (int t = tid; t < count; t += blockDim.x) dst[t] = stage[t];
+            }
+            __syncthreads();
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tc_fence_after();
+            tmem_dealloc(s_tmem, (uint32_t)A.tm_cols);
         }
     }
 }
@@ -248,10 +413,16 @@ static void make_plan(rascal_ctx* ctx) {
         return (size_t)chunk * sizeof(float4) + (size_t)chunk * (P.F_pad + P.Lp) * sizeof(float) +
                (size_t)chunk * (sizeof(float) + 2 * sizeof(int)) + (kMaxSpecies + 1 + kMaxLMax + 2 + P.F_pad) * sizeof(int) + 64;
     };
-    P.chunk = 64;
-    while (P.chunk > 16 && smem_for(P.chunk) > 110 * 1024) P.chunk /= 2;
+    P.chunk = 32;  // about 30 KB for n_max 12, l_max 9: four CTAs per SM
+    while (P.chunk > 8 && smem_for(P.chunk) > 56 * 1024) P.chunk /= 2;
     P.smem = smem_for(P.chunk);
     P.smem_ps = 0;
+}
+
+template <int GRAM>
+static int set_attr() {
+    RASCAL_CUDA(cudaFuncSetAttribute(k_expansion<GRAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    return RASCAL_OK;
 }
 
 int expansion_setup(rascal_ctx* ctx) {
@@ -269,7 +440,10 @@ int expansion_setup(rascal_ctx* ctx) {
     RASCAL_CUDA(cudaMemcpyAsync(ctx->d_tasks, tasks.data(), sizeof(int) * tasks.size(), cudaMemcpyHostToDevice, ctx->stream));
     RASCAL_CUDA(cudaMemcpyAsync(ctx->d_fmap, fmap.data(), sizeof(int) * fmap.size(), cudaMemcpyHostToDevice, ctx->stream));
     RASCAL_CUDA(upload_ylm_constants(ctx->stream));
-    RASCAL_CUDA(cudaFuncSetAttribute(k_expansion, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    int st;
+    if ((st = set_attr<kGramNone>()) || (st = set_attr<kGramSimt>()) || (st = set_attr<kGramBf16>()) ||
+        (st = set_attr<kGramTf32x3>()))
+        return st;
     RASCAL_CUDA(cudaStreamSynchronize(ctx->stream));
     return RASCAL_OK;
 }
@@ -278,6 +452,7 @@ static ExpArgs make_args(rascal_ctx* ctx, const rascal_system* sys, const int64_
                          const float* d_rij, float* d_coeffs) {
     const ExpPlan& P = ctx->plan;
     ExpArgs A;
+    std::memset(&A, 0, sizeof(A));
     A.offsets = d_offsets;
     A.nbr_j = d_nbr_j;
     A.rij = reinterpret_cast<const float4*>(d_rij);
@@ -308,7 +483,99 @@ static ExpArgs make_args(rascal_ctx* ctx, const rascal_system* sys, const int64_
     A.r_cut = (float)ctx->r_cut;
     A.width = (float)ctx->smooth_width;
     for (int l = 0; l < kMaxLMax + 2; ++l) A.lp[l] = P.lp[l];
+    A.gram_off = (int)align_up(P.smem, 1024);
     return A;
+}
+
+// Sets the fused power-spectrum part of the arguments; returns the total dynamic shared memory in *smem.
+static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs& A, size_t* smem, int* threads) {
+    const ExpPlan& P = ctx->plan;
+    const int Q = ctx->Q;
+    A.ps = d_ps;
+    A.layout = layout;
+    A.ps_norm = ctx->ps_norm;
+    A.Q = Q;
+    A.per_l = layout == RASCAL_LAYOUT_PACKED ? Q * (Q + 1) / 2 : Q * Q;
+    A.ps_stride = (int64_t)(ctx->l_max + 1) * A.per_l;
+    const size_t pair_region = (size_t)P.chunk * (P.F_pad + P.Lp);  // floats available for staging
+    const int L1 = ctx->l_max + 1;
+    *threads = P.threads;
+    size_t gram_bytes = 0;
+    size_t stage_need = 0;
+    if (mode == kGramSimt) {
+        A.Qp = (Q + 3) / 4 * 4;
+        gram_bytes = sizeof(float) * (size_t)ctx->n_lm * A.Qp;
+        A.ps_tasks = ctx->d_pstasks;
+        // groups of consecutive l (descending, the task order) whose blocks fit the staging area
+        const int Q4 = A.Qp / 4;
+        const int per_tile_l = Q4 * (Q4 + 1) / 2;
+        const size_t cap = std::max(pair_region, (size_t)A.per_l);
+        int g = 0, t = 0, l = ctx->l_max;
+        while (l >= 0) {
+            int n = 0;
+            while (l - n >= 0 && (size_t)(n + 1) * A.per_l <= cap) ++n;
+            A.g_hi[g] = l + 1;
+            A.g_lo[g] = l - n + 1;
+            A.g_tbeg[g] = t;
+            t += n * per_tile_l;
+            A.g_tend[g] = t;
+            stage_need = std::max(stage_need, (size_t)n * A.per_l);
+            l -= n;
+            ++g;
+        }
+        A.n_groups = g;
+    } else {
+        if (Q > 128) return set_error(RASCAL_E_UNSUPPORTED, "tensor-core power spectrum needs n_species*n_max <= 128");
+        const bool tf32 = mode == kGramTf32x3;
+        const int esz = tf32 ? 4 : 2, kstep = tf32 ? 8 : 16, e16 = 16 / esz;
+        A.N_mma = (Q + 15) / 16 * 16;
+        const int Qr = (Q + 7) / 8 * 8;
+        int off = 0, need = 0;
+        for (int l = 0; l <= ctx->l_max; ++l) {
+            const int kpad = (2 * l + 1 + kstep - 1) / kstep * kstep;
+            A.nk[l] = kpad / kstep;
+            A.sbo[l] = (kpad / e16) * 128;
+            A.tile_off[l] = off;
+            need = std::max(need, off + 16 * A.sbo[l]);  // M = 128 rows read from the tile's start
+            off += (Qr / 8) * A.sbo[l];
+        }
+        const int hi_bytes = (std::max(off, need) + 1023) / 1024 * 1024;
+        A.lo_off = tf32 ? hi_bytes : 0;
+        A.tiles_bytes = tf32 ? 2 * hi_bytes : hi_bytes;
+        gram_bytes = (size_t)A.tiles_bytes;
+        A.tm_cols = A.N_mma <= 64 ? 128 : 256;
+        const int per_group = A.tm_cols / A.N_mma;
+        const size_t cap = std::max(pair_region, (size_t)A.per_l);
+        int g = 0;
+        for (int l = 0; l < L1;) {
+            int n = 0;
+            while (l + n < L1 && n < per_group && (size_t)(n + 1) * A.per_l <= cap) ++n;
+            A.g_lo[g] = l;
+            A.g_hi[g] = l + n;
+            stage_need = std::max(stage_need, (size_t)n * A.per_l);
+            l += n;
+            ++g;
+        }
+        A.n_groups = g;
+        *threads = std::max(*threads, 128);  // the epilogue reads TMEM lanes 0..127 with warps 0..3
+    }
+    // the staging area aliases the pair buffers; grow the pair region if one group needs more
+    size_t exp_bytes = P.smem;
+    const size_t stage_bytes_avail = pair_region * sizeof(float);
+    if (stage_need * sizeof(float) > stage_bytes_avail) exp_bytes += stage_need * sizeof(float) - stage_bytes_avail;
+    A.stage_floats = (int)std::max(stage_need, pair_region);
+    // the staging may run over the (then unused) small arrays behind the pair buffers, up to the gram region
+    A.gram_off = (int)align_up(exp_bytes, 1024);
+    *smem = (size_t)A.gram_off + gram_bytes;
+    if (*smem > 220 * 1024) return set_error(RASCAL_E_UNSUPPORTED, "fused power spectrum needs %zu bytes of shared memory", *smem);
+    return RASCAL_OK;
+}
+
+template <int GRAM>
+static int launch_expansion(rascal_ctx* ctx, const ExpArgs& A, int n_atoms, int threads, size_t smem) {
+    k_expansion<GRAM><<<n_atoms, threads, smem, ctx->stream>>>(A);
+    RASCAL_LAUNCH_CHECK("k_expansion");
+    return RASCAL_OK;
 }
 
 }  // namespace rascal
@@ -324,7 +591,25 @@ extern "C" int rascal_spherical_expansion(rascal_ctx* ctx, const rascal_system* 
     if (sys->n_atoms == 0) return RASCAL_OK;
     if (!d_offsets || !d_nbr_j || !d_rij || !d_coeffs) return set_error(RASCAL_E_ARG, "NULL device pointer");
     const ExpArgs A = make_args(ctx, sys, d_offsets, d_nbr_j, d_rij, d_coeffs);
-    k_expansion<<<sys->n_atoms, ctx->plan.threads, ctx->plan.smem, ctx->stream>>>(A);
-    RASCAL_LAUNCH_CHECK("k_expansion");
-    return RASCAL_OK;
+    return launch_expansion<kGramNone>(ctx, A, sys->n_atoms, ctx->plan.threads, ctx->plan.smem);
+}
+
+extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,
+                           const float* d_rij, int precision, int layout, float* d_coeffs, float* d_ps) {
+    clear_error();
+    if (!ctx) return set_error(RASCAL_E_ARG, "NULL context");
+    int st = validate_system(ctx, sys);
+    if (st) return st;
+    if (layout != RASCAL_LAYOUT_PACKED && layout != RASCAL_LAYOUT_FULL) return set_error(RASCAL_E_ARG, "unknown layout");
+    if (precision < RASCAL_PS_FP32 || precision > RASCAL_PS_TF32X3) return set_error(RASCAL_E_ARG, "unknown precision");
+    if (sys->n_atoms == 0) return RASCAL_OK;
+    if (!d_offsets || !d_nbr_j || !d_rij || !d_coeffs || !d_ps) return set_error(RASCAL_E_ARG, "NULL device pointer");
+    ExpArgs A = make_args(ctx, sys, d_offsets, d_nbr_j, d_rij, d_coeffs);
+    const int mode = precision == RASCAL_PS_FP32 ? kGramSimt : (precision == RASCAL_PS_BF16 ? kGramBf16 : kGramTf32x3);
+    size_t smem;
+    int threads;
+    if ((st = make_gram(ctx, mode, layout, d_ps, A, &smem, &threads))) return st;
+    if (mode == kGramSimt) return launch_expansion<kGramSimt>(ctx, A, sys->n_atoms, threads, smem);
+    if (mode == kGramBf16) return launch_expansion<kGramBf16>(ctx, A, sys->n_atoms, threads, smem);
+    return launch_expansion<kGramTf32x3>(ctx, A, sys->n_atoms, threads, smem);
 }

@@ -400,10 +400,3 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
     RASCAL_LAUNCH_CHECK("k_gradients");
     return RASCAL_OK;
 }
-
-extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,
-                           const float* d_rij, int layout, float* d_coeffs, float* d_ps) {
-    int st = rascal_spherical_expansion(ctx, sys, d_offsets, d_nbr_j, d_rij, d_coeffs);
-    if (st) return st;
-    return rascal_power_spectrum(ctx, sys->n_atoms, d_coeffs, RASCAL_PS_FP32, layout, d_ps);
-}

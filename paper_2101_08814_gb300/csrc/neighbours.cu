@@ -276,34 +276,54 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(
     }
     int count = 0;
     unsigned local_flags = 0;
-    for (int d0 = -S.reach[0]; d0 <= S.reach[0]; ++d0)
-        for (int d1 = -S.reach[1]; d1 <= S.reach[1]; ++d1)
-            for (int d2 = -S.reach[2]; d2 <= S.reach[2]; ++d2) {
-                const int dd[3] = {d0, d1, d2};
-                int tb[3], t[3];
-                bool valid = true;
+    // Flattened walk over the stencil: up to 32 stencil bins at a time, one per lane, their candidate counts
+    // prefix-summed across the warp, then 32 candidates per iteration with each lane locating its bin by a
+    // binary search over the prefix (all loop bounds warp-uniform).
+    __shared__ int64_t s_beg[kPairWarps][32];
+    __shared__ int4 s_t[kPairWarps][32];
+    __shared__ float4 s_T[kPairWarps][32];
+    __shared__ float4 s_Th[kPairWarps][FILL ? 32 : 1];
+    __shared__ float4 s_Tl[kPairWarps][FILL ? 32 : 1];
+    const int w0 = 2 * S.reach[0] + 1, w1 = 2 * S.reach[1] + 1, w2 = 2 * S.reach[2] + 1;
+    const int n_st = w0 * w1 * w2;
+    for (int g0 = 0; g0 < n_st; g0 += 32) {
+        const int e = g0 + lane;
+        int cnt = 0;
+        if (e < n_st) {
+            const int dd[3] = {e / (w1 * w2) - S.reach[0], (e / w2) % w1 - S.reach[1], e % w2 - S.reach[2]};
+            int tb[3], t[3];
+            bool valid = true;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const int x = bci[k] + dd[k];
-                    if (S.pbc[k]) {
-                        t[k] = floordiv(x, S.nb[k]);
-                        tb[k] = x - t[k] * S.nb[k];
-                    } else {
-                        t[k] = 0;
-                        tb[k] = x;
-                        if (x < 0 || x >= S.nb[k]) valid = false;
-                    }
+            for (int k = 0; k < 3; ++k) {
+                const int x = bci[k] + dd[k];
+                if (S.pbc[k]) {
+                    t[k] = floordiv(x, S.nb[k]);
+                    tb[k] = x - t[k] * S.nb[k];
+                } else {
+                    t[k] = 0;
+                    tb[k] = x;
+                    if (x < 0 || x >= S.nb[k]) valid = false;
                 }
-                if (!valid) continue;
-                const bool self_image = (t[0] == 0 && t[1] == 0 && t[2] == 0);
-                // image translation T = t H in FP32 (filter) and double-single (output vector)
-                float Tf[3], Th[3], Tl[3];
+            }
+            const int64_t bin = binbase[s] + (tb[0] * S.nb[1] + tb[1]) * S.nb[2] + tb[2];
+            if (bin < 0 || bin >= nbins_cap) valid = false;  // inconsistent offsets, already flagged
+            if (valid) {
+                const int64_t beg = bin_start[bin];
+                cnt = (int)(bin_start[bin + 1] - beg);
+                s_beg[warp][lane] = beg;
+                s_t[warp][lane] = make_int4(t[0], t[1], t[2], (t[0] == 0 && t[1] == 0 && t[2] == 0) ? 1 : 0);
+                float Tf[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     // explicit roundings: the count and fill passes must take identical decisions
                     Tf[c] = __fadd_rn(__fadd_rn(__fmul_rn((float)t[0], S.hhi[c]), __fmul_rn((float)t[1], S.hhi[3 + c])),
                                       __fmul_rn((float)t[2], S.hhi[6 + c]));
-                    if (FILL) {
+                }
+                s_T[warp][lane] = make_float4(Tf[0], Tf[1], Tf[2], 0.0f);
+                if (FILL) {
+                    float Th[3], Tl[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
                         float sh = 0.0f, sl = 0.0f;
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
@@ -317,71 +337,94 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(
                         Th[c] = sh;
                         Tl[c] = sl;
                     }
-                }
-                const int64_t bin = binbase[s] + (tb[0] * S.nb[1] + tb[1]) * S.nb[2] + tb[2];
-                if (bin < 0 || bin >= nbins_cap) continue;  // inconsistent offsets, already flagged
-                const int64_t beg = bin_start[bin], end = bin_start[bin + 1];
-                for (int64_t base = beg; base < end; base += 32) {
-                    const int64_t c = base + lane;
-                    bool accept = false;
-                    int j = -1;
-                    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (c < end) {
-                        q = sorted_hi[c];
-                        j = __float_as_int(q.w);
-                        const float dx = __fsub_rn(__fadd_rn(q.x, Tf[0]), phi.x);
-                        const float dy = __fsub_rn(__fadd_rn(q.y, Tf[1]), phi.y);
-                        const float dz = __fsub_rn(__fadd_rn(q.z, Tf[2]), phi.z);
-                        const float dsq = fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
-                        if (!(j == i && self_image)) {
-                            if (dsq < thr_lo2) {
-                                accept = true;
-                            } else if (dsq <= thr_hi2) {
-                                const int4 wj = atom_wrap[j];
-                                const int n[3] = {t[0] - wj.x + wi.x, t[1] - wj.y + wi.y, t[2] - wj.z + wi.z};
-                                accept = exact_d2(pos, i, j, S.H, n) < rc2;
-                            }
-                            if (accept && dsq < thr_tiny2) {
-                                const int4 wj = atom_wrap[j];
-                                const int n[3] = {t[0] - wj.x + wi.x, t[1] - wj.y + wi.y, t[2] - wj.z + wi.z};
-                                if (exact_d2(pos, i, j, S.H, n) < 1e-12) local_flags |= kFlagGeometry;
-                            }
-                        }
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, accept);
-                    if (accept) {
-                        const int4 wj = atom_wrap[j];
-                        const int n[3] = {t[0] - wj.x + wi.x, t[1] - wj.y + wi.y, t[2] - wj.z + wi.z};
-                        if (n[0] < -kMaxShift || n[0] > kMaxShift || n[1] < -kMaxShift || n[1] > kMaxShift ||
-                            n[2] < -kMaxShift || n[2] > kMaxShift)
-                            local_flags |= kFlagShiftRange;
-                        if (FILL) {
-                            const int slot = count + __popc(m & ((1u << lane) - 1u));
-                            if (slot < seg_cnt) {
-                                const float4 qlo = atom_lo[j];
-                                const float pj[3] = {q.x, q.y, q.z}, pjl[3] = {qlo.x, qlo.y, qlo.z};
-                                const float pi_[3] = {phi.x, phi.y, phi.z}, pil[3] = {plo.x, plo.y, plo.z};
-                                float v[3];
-#pragma unroll
-                                for (int cc = 0; cc < 3; ++cc) {
-                                    float s1, e1, s2, e2;
-                                    two_sum(pj[cc], Th[cc], s1, e1);
-                                    e1 += pjl[cc] + Tl[cc];
-                                    two_sum(s1, -pi_[cc], s2, e2);
-                                    e2 += e1 - pil[cc];
-                                    v[cc] = s2 + e2;
-                                }
-                                const float rr = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                                const int nc[3] = {min(max(n[0], -kMaxShift), kMaxShift), min(max(n[1], -kMaxShift), kMaxShift),
-                                                   min(max(n[2], -kMaxShift), kMaxShift)};
-                                keys[slot] = pair_key(j, nc);
-                                vecs[slot] = make_float4(v[0], v[1], v[2], rr);
-                            }
-                        }
-                    }
-                    count += __popc(m);
+                    s_Th[warp][FILL ? lane : 0] = make_float4(Th[0], Th[1], Th[2], 0.0f);
+                    s_Tl[warp][FILL ? lane : 0] = make_float4(Tl[0], Tl[1], Tl[2], 0.0f);
                 }
             }
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        for (int base = 0; base < total; base += 32) {
+            const int cidx = base + lane;
+            // entry k of this candidate: number of entries whose inclusive prefix is <= cidx
+            int k = 0;
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, incl, k + st - 1);
+                if (v <= cidx) k += st;
+            }
+            const int excl_k = __shfl_sync(0xffffffffu, incl, k) - __shfl_sync(0xffffffffu, cnt, k);
+            bool accept = false;
+            int j = -1;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            int4 tt = make_int4(0, 0, 0, 0);
+            if (cidx < total) {
+                tt = s_t[warp][k];
+                const float4 Tf = s_T[warp][k];
+                q = sorted_hi[s_beg[warp][k] + (cidx - excl_k)];
+                j = __float_as_int(q.w);
+                const float dx = __fsub_rn(__fadd_rn(q.x, Tf.x), phi.x);
+                const float dy = __fsub_rn(__fadd_rn(q.y, Tf.y), phi.y);
+                const float dz = __fsub_rn(__fadd_rn(q.z, Tf.z), phi.z);
+                const float dsq = fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
+                if (!(j == i && tt.w)) {
+                    if (dsq < thr_lo2) {
+                        accept = true;
+                    } else if (dsq <= thr_hi2) {
+                        const int4 wj = atom_wrap[j];
+                        const int n[3] = {tt.x - wj.x + wi.x, tt.y - wj.y + wi.y, tt.z - wj.z + wi.z};
+                        accept = exact_d2(pos, i, j, S.H, n) < rc2;
+                    }
+                    if (accept && dsq < thr_tiny2) {
+                        const int4 wj = atom_wrap[j];
+                        const int n[3] = {tt.x - wj.x + wi.x, tt.y - wj.y + wi.y, tt.z - wj.z + wi.z};
+                        if (exact_d2(pos, i, j, S.H, n) < 1e-12) local_flags |= kFlagGeometry;
+                    }
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, accept);
+            if (accept) {
+                const int4 wj = atom_wrap[j];
+                const int n[3] = {tt.x - wj.x + wi.x, tt.y - wj.y + wi.y, tt.z - wj.z + wi.z};
+                if (n[0] < -kMaxShift || n[0] > kMaxShift || n[1] < -kMaxShift || n[1] > kMaxShift || n[2] < -kMaxShift ||
+                    n[2] > kMaxShift)
+                    local_flags |= kFlagShiftRange;
+                if (FILL) {
+                    const int slot = count + __popc(m & ((1u << lane) - 1u));
+                    if (slot < seg_cnt) {
+                        const float4 qlo = atom_lo[j];
+                        const float4 Th4 = s_Th[warp][FILL ? k : 0], Tl4 = s_Tl[warp][FILL ? k : 0];
+                        const float Th[3] = {Th4.x, Th4.y, Th4.z}, Tl[3] = {Tl4.x, Tl4.y, Tl4.z};
+                        const float pj[3] = {q.x, q.y, q.z}, pjl[3] = {qlo.x, qlo.y, qlo.z};
+                        const float pi_[3] = {phi.x, phi.y, phi.z}, pil[3] = {plo.x, plo.y, plo.z};
+                        float v[3];
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) {
+                            float s1, e1, s2, e2;
+                            two_sum(pj[cc], Th[cc], s1, e1);
+                            e1 += pjl[cc] + Tl[cc];
+                            two_sum(s1, -pi_[cc], s2, e2);
+                            e2 += e1 - pil[cc];
+                            v[cc] = s2 + e2;
+                        }
+                        const float rr = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                        const int nc[3] = {min(max(n[0], -kMaxShift), kMaxShift), min(max(n[1], -kMaxShift), kMaxShift),
+                                           min(max(n[2], -kMaxShift), kMaxShift)};
+                        keys[slot] = pair_key(j, nc);
+                        vecs[slot] = make_float4(v[0], v[1], v[2], rr);
+                    }
+                }
+            }
+            count += __popc(m);
+        }
+        __syncwarp();
+    }
     if (local_flags) atomicOr(flags, local_flags);
     if (!FILL) {
         if (lane == 0) {

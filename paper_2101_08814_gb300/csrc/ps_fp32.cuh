@@ -9,60 +9,69 @@
 
 namespace rascal {
 
-__device__ inline int64_t packed_index(int q1, int q2, int Q) {  // q1 <= q2
+__device__ __host__ inline int64_t packed_index(int q1, int q2, int Q) {  // q1 <= q2
     return (int64_t)q1 * Q - (int64_t)q1 * (q1 - 1) / 2 + (q2 - q1);
+}
+
+__device__ inline void gram_tile_fp32(const float* __restrict__ CT, int Qp, int l, int t1, int t2, float (&acc)[4][4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+    const float* row = CT + (size_t)(l * l) * Qp;
+    for (int s = 0; s <= 2 * l; ++s, row += Qp) {
+        const float4 a = *reinterpret_cast<const float4*>(row + 4 * t1);
+        const float4 b = *reinterpret_cast<const float4*>(row + 4 * t2);
+        const float aa[4] = {a.x, a.y, a.z, a.w}, bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(aa[u], bb[v], acc[u][v]);
+    }
+}
+
+// writes k * tile into the l-block o (PACKED: q1 <= q2 only; FULL: both triangles)
+__device__ inline void store_tile_fp32(float* __restrict__ o, int Q, int layout, int t1, int t2, float k,
+                                       const float (&acc)[4][4]) {
+    if (layout == RASCAL_LAYOUT_PACKED) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q1 = 4 * t1 + u;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int q2 = 4 * t2 + v;
+                if (q1 <= q2 && q2 < Q) o[packed_index(q1, q2, Q)] = k * acc[u][v];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q1 = 4 * t1 + u;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int q2 = 4 * t2 + v;
+                if (q1 < Q && q2 < Q) {
+                    o[(int64_t)q1 * Q + q2] = k * acc[u][v];
+                    if (t1 != t2) o[(int64_t)q2 * Q + q1] = k * acc[u][v];
+                }
+            }
+        }
+    }
 }
 
 // tasks: packed (l | t1 << 8 | t2 << 16); out points at this centre's p block
 __device__ inline void ps_gram_fp32(const float* __restrict__ CT, int Qp, int Q, int l_max, int ps_norm,
                                     const int* __restrict__ tasks, int n_tasks, int layout, float* __restrict__ out) {
-    const int Qpk = Q * (Q + 1) / 2;
+    const int64_t per_l = layout == RASCAL_LAYOUT_PACKED ? (int64_t)Q * (Q + 1) / 2 : (int64_t)Q * Q;
     for (int t = threadIdx.x; t < n_tasks; t += blockDim.x) {
         const int packed = __ldg(&tasks[t]);
         const int l = packed & 0xff, t1 = (packed >> 8) & 0xff, t2 = (packed >> 16) & 0xff;
         float acc[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
-        const float* row = CT + (size_t)(l * l) * Qp;
-        for (int s = 0; s <= 2 * l; ++s, row += Qp) {
-            const float4 a = *reinterpret_cast<const float4*>(row + 4 * t1);
-            const float4 b = *reinterpret_cast<const float4*>(row + 4 * t2);
-            const float aa[4] = {a.x, a.y, a.z, a.w}, bb[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(aa[u], bb[v], acc[u][v]);
-        }
+        gram_tile_fp32(CT, Qp, l, t1, t2, acc);
         const float k = ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f;
-        if (layout == RASCAL_LAYOUT_PACKED) {
-            float* o = out + (int64_t)l * Qpk;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q1 = 4 * t1 + u;
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int q2 = 4 * t2 + v;
-                    if (q1 <= q2 && q2 < Q) o[packed_index(q1, q2, Q)] = k * acc[u][v];
-                }
-            }
-        } else {
-            float* o = out + (int64_t)l * Q * Q;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q1 = 4 * t1 + u;
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int q2 = 4 * t2 + v;
-                    if (q1 < Q && q2 < Q) {
-                        o[(int64_t)q1 * Q + q2] = k * acc[u][v];
-                        if (t1 != t2) o[(int64_t)q2 * Q + q1] = k * acc[u][v];
-                    }
-                }
-            }
-        }
+        store_tile_fp32(out + l * per_l, Q, layout, t1, t2, k, acc);
     }
+    (void)l_max;
 }
 
 }  // namespace rascal

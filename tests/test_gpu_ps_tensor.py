@@ -1,0 +1,89 @@
+"""tcgen05 power spectrum (BF16 and TF32x3) against the FP64 Gram of the same coefficients.
+
+Tolerances per (centre, l) block:
+* TF32x3 and FP32: max |gpu - oracle| / max |oracle| <= 1e-5 (the hi/lo split leaves about 2^-21 per product);
+* BF16 inputs: bfloat16 has 8 significant bits, unit roundoff u = 2^-8, so a product of two rounded inputs is off by
+  up to 2u = 2^-7 relative; the block max-relative error is held to 2^-7 and the block's relative Frobenius-norm
+  error ||dp|| / ||p|| to the 5e-3 target (the FP64 Gram of bf16-rounded inputs reaches 4.6e-3 on these workloads).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import soap as osoap  # noqa: E402
+from synth import System, config_batch, config_tiny, random_cell_atoms  # noqa: E402
+from tests.gpu_common import block_rel_err, ps_blocks  # noqa: E402
+
+TOL = {"bf16": 5e-3, "tf32x3": 1e-5, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def rg():
+    import paper_2101_08814_gb300 as rg
+
+    return rg
+
+
+def _system(n_species, n_max, l_max, r_cut=5.0, n_atoms=160, seed=3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = (n_atoms / 0.05) ** (1 / 3)
+    pos = random_cell_atoms(n_atoms, np.eye(3) * L, 1.6, rng)
+    labels = list(range(1, n_species + 1))
+    spe = np.asarray(labels, np.int32)[rng.integers(0, n_species, n_atoms)]
+    return System(pos, spe, (np.eye(3) * L)[None], np.ones((1, 3), np.int32), np.array([0, n_atoms], np.int32),
+                  dict(r_cut=r_cut, sigma=0.5, n_max=n_max, l_max=l_max, smooth_width=0.5, species=labels))
+
+
+def _check(rg, s, layouts=("packed", "full"), centres=None):
+    calc = rg.SoapCalculator(**s.hypers)
+    ds = rg.DeviceSystem.from_numpy(s)
+    pairs = calc.neighbours(ds)
+    c = calc.spherical_expansion(ds, pairs)
+    h = osoap.Hypers(**s.hypers)
+    sel = np.arange(s.n_atoms) if centres is None else np.asarray(centres)
+    c_np = c.cpu().numpy()[sel].astype(np.float64)
+    for layout in layouts:
+        ref = osoap.power_spectrum(c_np, h, layout)
+        for prec, fused in [(p_, f_) for p_ in ("bf16", "tf32x3", "fp32") for f_ in (False, True)]:
+            try:
+                if fused:
+                    c2, p = calc.soap(ds, pairs, layout=layout, precision=prec)
+                    calc.sync()
+                    assert np.array_equal(c2.cpu().numpy(), c.cpu().numpy())
+                else:
+                    p = calc.power_spectrum(c, precision=prec, layout=layout)
+                    calc.sync()
+            except rg.RascalError as e:
+                # the TF32 hi/lo operand tiles of n_species*n_max = 128, l_max = 12 exceed shared memory: the
+                # library refuses them with RASCAL_E_UNSUPPORTED instead of running
+                assert e.code == rg._lib.RASCAL_E_UNSUPPORTED and prec == "tf32x3" and h.q > 96, (prec, fused, str(e))
+                continue
+            got = p.cpu().numpy()[sel]
+            gb, rb = ps_blocks(got, h.l_max), ref.reshape(len(sel), h.l_max + 1, -1)
+            err = block_rel_err(gb, rb, 2)
+            if prec == "bf16":
+                assert err <= 2.0 ** -7, (layout, prec, err)
+                fro = np.sqrt(np.sum((gb - rb) ** 2, axis=-1) / np.maximum(np.sum(rb ** 2, axis=-1), 1e-300))
+                assert np.max(fro) <= 5e-3, (layout, prec, np.max(fro))
+            else:
+                assert err <= TOL[prec], (layout, prec, err)
+            assert np.all(np.isfinite(got))
+
+
+def test_tiny_single_species(rg):
+    _check(rg, config_tiny())
+
+
+def test_q30_needs_padded_columns(rg):
+    _check(rg, _system(3, 10, 8, r_cut=6.0))
+
+
+def test_q128_many_l_groups(rg):
+    _check(rg, _system(8, 16, 12, r_cut=6.0, n_atoms=120), centres=[0, 50, 119])
+
+
+def test_batch_full_size_sampled(rg):
+    s = config_batch()
+    rng = np.random.default_rng(2)
+    _check(rg, s, layouts=("packed",), centres=np.concatenate([[0, s.n_atoms - 1], rng.choice(s.n_atoms, 30, replace=False)]))
