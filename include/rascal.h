@@ -30,6 +30,7 @@
 #ifndef RASCAL_H
 #define RASCAL_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -135,6 +136,28 @@ int rascal_sync(rascal_ctx* ctx);
  * RASCAL_E_UNSUPPORTED. */
 int rascal_neighbours(rascal_ctx* ctx, const rascal_system* sys, int64_t capacity, int64_t* d_offsets,
                       int* d_nbr_j, int* d_shift, float* d_rij, int64_t* n_pairs);
+
+/* rascal_neighbours for callers that cannot allocate device memory while they run (no counterpart in the paper,
+ * which describes a serial CPU library). Some callers cannot call cudaMalloc: an MD engine that has reserved the
+ * device memory through its own pool allocator, or a time-stepping loop that must not hit cudaMalloc / cudaFree
+ * because they synchronise the whole device. This entry point takes the same arguments, launches the same kernels
+ * and produces the same output, but carves every scratch buffer out of one file-scope device array of
+ * rascal_neighbours_static_limit() bytes (32 MiB) instead of the context's scratch arena; it calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   - The array is part of the library's device image: every GPU that loads the library holds it until exit.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress, with that device
+ *     current) and caches it; make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents (what must start at zero is cleared
+ *     on every call). Calls that overlap on the GPU (other streams, other contexts, other host threads) race on
+ *     it: serialise them.
+ *   - Limits: a system needing more scratch than the array (about 116 bytes per atom plus 360 per structure:
+ *     some 280k atoms in one cell) is refused with RASCAL_E_UNSUPPORTED before anything runs; so is a centre with
+ *     more than 256 neighbours, which rascal_neighbours sorts in an allocated overflow buffer.
+ * Synchronises the stream once, like rascal_neighbours. */
+int rascal_neighbours_noalloc(rascal_ctx* ctx, const rascal_system* sys, int64_t capacity, int64_t* d_offsets,
+                              int* d_nbr_j, int* d_shift, float* d_rij, int64_t* n_pairs);
+/* Size in bytes of the device array that rascal_neighbours_noalloc uses for scratch. */
+size_t rascal_neighbours_static_limit(void);
 
 /* Spherical expansion coefficients (Eq. spherical_expansion_coefficients_gaussians) of every centre from a pair
  * list made by rascal_neighbours for the same system. d_coeffs: [n_atoms][n_species][n_max][(l_max+1)^2]. */

@@ -85,6 +85,9 @@ _SIGNATURES = {
     "rascal_sync": (C.c_int, [C.c_void_p]),
     "rascal_neighbours": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.POINTER(C.c_int64)]),
+    "rascal_neighbours_noalloc": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_int64, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
+    "rascal_neighbours_static_limit": (C.c_size_t, []),
     "rascal_spherical_expansion": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p]),
     "rascal_power_spectrum": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),

@@ -147,6 +147,10 @@ inline size_t carve_bytes(Ts... sizes) {
 // device-wide exclusive scan: out[0..n] with out[n] = total; in and out may alias. Input int32 or int64.
 int scan_exclusive(const int* in, int64_t* out, int64_t n, cudaStream_t stream, Arena& scratch);
 int scan_exclusive(const int64_t* in, int64_t* out, int64_t n, cudaStream_t stream, Arena& scratch);
+// the same with a caller-provided tile-sum buffer of scan_tile_sums_len(n) words (no allocation)
+int64_t scan_tile_sums_len(int64_t n);
+int scan_exclusive_into(const int* in, int64_t* out, int64_t n, cudaStream_t stream, int64_t* sums);
+int scan_exclusive_into(const int64_t* in, int64_t* out, int64_t n, cudaStream_t stream, int64_t* sums);
 
 int validate_system(const rascal_ctx* ctx, const rascal_system* sys);
 

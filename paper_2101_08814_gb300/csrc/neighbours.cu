@@ -17,6 +17,9 @@
 // formula d = (r_j - r_i) + ((n1 h1 + n2 h2) + n3 h3), d.d = (dx dx + dy dy) + dz dz < r_cut r_cut, each
 // operation rounded on its own (__dadd_rn / __dmul_rn, no contraction). The output vector r_ji is computed in
 // double-single arithmetic (error-free FP32 transforms) and rounded once to FP32.
+#include <algorithm>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace rascal {
@@ -567,6 +570,132 @@ extern "C" int rascal_neighbours(rascal_ctx* ctx, const rascal_system* sys, int6
                                                                atom_struct, atom_cell, atom_wrap, atom_hi, atom_lo, rc2,
                                                                nbins_cap, d_offsets, nullptr, d_nbr_j, d_shift,
                                                                reinterpret_cast<float4*>(d_rij), ovf_keys, ovf_vec,
+                                                               ctx->d_flags);
+    RASCAL_LAUNCH_CHECK("k_pairs<fill>");
+    return RASCAL_OK;
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// Neighbour search that allocates nothing: the same kernels as rascal_neighbours, with all scratch carved out of
+// one file-scope device array. The array is a module global, so every GPU that loads the library holds it until
+// the process exits. Its device address is looked up once per device (cudaGetSymbolAddress with that device
+// current, on the first call made on it) and cached; all calls on a device share the array.
+// ---------------------------------------------------------------------------------------------------------
+namespace rascal {
+
+constexpr size_t kStaticNbrScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_nbr_scratch[kStaticNbrScratchBytes];
+constexpr int kMaxDevices = 64;
+static void* g_nbr_scratch_addr[kMaxDevices];
+static std::mutex g_nbr_scratch_mu;
+
+static int static_nbr_scratch(void** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(RASCAL_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(RASCAL_E_UNSUPPORTED, "device ordinal %d above %d", dev, kMaxDevices - 1);
+    std::lock_guard<std::mutex> lock(g_nbr_scratch_mu);
+    if (!g_nbr_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_nbr_scratch);
+        if (e != cudaSuccess || !p)
+            return set_error(RASCAL_E_CUDA, "cudaGetSymbolAddress of the static neighbour scratch: %s", cudaGetErrorString(e));
+        g_nbr_scratch_addr[dev] = p;
+    }
+    *out = g_nbr_scratch_addr[dev];
+    return RASCAL_OK;
+}
+
+}  // namespace rascal
+
+extern "C" size_t rascal_neighbours_static_limit(void) { return rascal::kStaticNbrScratchBytes; }
+
+extern "C" int rascal_neighbours_noalloc(rascal_ctx* ctx, const rascal_system* sys, int64_t capacity, int64_t* d_offsets,
+                                         int* d_nbr_j, int* d_shift, float* d_rij, int64_t* n_pairs) {
+    clear_error();
+    if (!ctx) return set_error(RASCAL_E_ARG, "NULL context");
+    int st = validate_system(ctx, sys);
+    if (st) return st;
+    if (!d_offsets || !n_pairs || capacity < 0) return set_error(RASCAL_E_ARG, "NULL offsets / n_pairs or negative capacity");
+    const int N = sys->n_atoms, n_s = sys->n_structures;
+    cudaStream_t stream = ctx->stream;
+    *n_pairs = 0;
+    if (N == 0) {
+        RASCAL_CUDA(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), stream));
+        return RASCAL_OK;
+    }
+    const int64_t nbins_cap = 2LL * N + 8LL * n_s;
+    const int64_t sums_len = std::max(scan_tile_sums_len(n_s), std::max(scan_tile_sums_len(nbins_cap), scan_tile_sums_len(N)));
+    const size_t bytes = carve_bytes(sizeof(StructInfo) * n_s, sizeof(int) * (n_s + 1), sizeof(int64_t) * (n_s + 1),
+                                     sizeof(int) * nbins_cap, sizeof(int64_t) * (nbins_cap + 1), sizeof(int) * N,
+                                     sizeof(int) * N, sizeof(int) * N, sizeof(int4) * N, sizeof(int4) * N,
+                                     sizeof(float4) * N, sizeof(float4) * N, sizeof(float4) * N, sizeof(int) * 4,
+                                     sizeof(int64_t) * sums_len);
+    if (bytes > kStaticNbrScratchBytes)
+        return set_error(RASCAL_E_UNSUPPORTED,
+                         "this system needs %zu bytes of neighbour scratch; the no-allocation entry point holds %zu "
+                         "(about 116 bytes per atom and 360 per structure): use rascal_neighbours",
+                         bytes, kStaticNbrScratchBytes);
+    void* base = nullptr;
+    if ((st = static_nbr_scratch(&base))) return st;
+    Carver cv(base);
+    StructInfo* info = cv.take<StructInfo>(n_s);
+    int* nbins = cv.take<int>(n_s + 1);
+    int64_t* binbase = cv.take<int64_t>(n_s + 1);
+    int* bin_count = cv.take<int>(nbins_cap);
+    int64_t* bin_start = cv.take<int64_t>(nbins_cap + 1);
+    int* atom_bin = cv.take<int>(N);
+    int* atom_rank = cv.take<int>(N);
+    int* atom_struct = cv.take<int>(N);
+    int4* atom_cell = cv.take<int4>(N);
+    int4* atom_wrap = cv.take<int4>(N);
+    float4* atom_hi = cv.take<float4>(N);
+    float4* atom_lo = cv.take<float4>(N);
+    float4* sorted_hi = cv.take<float4>(N);
+    int* max_count = cv.take<int>(4);
+    int64_t* sums = cv.take<int64_t>(sums_len);
+
+    // the array keeps the previous call's contents: the bin counters and the maximum must start at zero
+    RASCAL_CUDA(cudaMemsetAsync(bin_count, 0, sizeof(int) * nbins_cap, stream));
+    RASCAL_CUDA(cudaMemsetAsync(max_count, 0, sizeof(int), stream));
+    k_struct_setup<<<(unsigned)div_up(n_s, 128), 128, 0, stream>>>(n_s, N, sys->d_struct_offsets, sys->d_cells, sys->d_pbc,
+                                                                 ctx->r_cut, info, nbins, ctx->d_flags);
+    RASCAL_LAUNCH_CHECK("k_struct_setup");
+    if ((st = scan_exclusive_into(nbins, binbase, n_s, stream, sums))) return st;
+    k_atom_bin<<<(unsigned)div_up(N, 256), 256, 0, stream>>>(N, n_s, nbins_cap, sys->d_struct_offsets, sys->d_positions,
+                                                           sys->d_species, ctx->d_lut, info, binbase, bin_count, atom_bin,
+                                                           atom_rank, atom_struct, atom_cell, atom_wrap, atom_hi, atom_lo,
+                                                           ctx->d_flags);
+    RASCAL_LAUNCH_CHECK("k_atom_bin");
+    if ((st = scan_exclusive_into(bin_count, bin_start, nbins_cap, stream, sums))) return st;
+    k_atom_scatter<<<(unsigned)div_up(N, 256), 256, 0, stream>>>(N, atom_bin, atom_rank, bin_start, atom_hi, sorted_hi);
+    RASCAL_LAUNCH_CHECK("k_atom_scatter");
+    k_struct_thresholds<<<(unsigned)div_up(n_s, 128), 128, 0, stream>>>(n_s, ctx->r_cut, info);
+    RASCAL_LAUNCH_CHECK("k_struct_thresholds");
+    const double rc2 = ctx->r_cut * ctx->r_cut;
+    const unsigned pair_blocks = (unsigned)div_up(N, kPairWarps);
+    k_pairs<false><<<pair_blocks, kPairWarps * 32, 0, stream>>>(N, sys->d_positions, info, binbase, bin_start, sorted_hi,
+                                                                atom_struct, atom_cell, atom_wrap, atom_hi, atom_lo, rc2,
+                                                                nbins_cap, d_offsets, max_count, nullptr, nullptr, nullptr,
+                                                                nullptr, nullptr, ctx->d_flags);
+    RASCAL_LAUNCH_CHECK("k_pairs<count>");
+    if ((st = scan_exclusive_into(d_offsets, d_offsets, N, stream, sums))) return st;
+    RASCAL_CUDA(cudaMemcpyAsync(ctx->h_pinned, d_offsets + N, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    RASCAL_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, max_count, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    if ((st = check_flags(ctx))) return st;  // synchronises the stream
+    const int64_t P = ctx->h_pinned[0];
+    const int maxc = *reinterpret_cast<int*>(ctx->h_pinned + 1);
+    *n_pairs = P;
+    if (P > capacity) return set_error(RASCAL_E_CAPACITY, "pair capacity %lld < required %lld", (long long)capacity, (long long)P);
+    if (P == 0) return RASCAL_OK;
+    if (!d_nbr_j || !d_shift || !d_rij) return set_error(RASCAL_E_ARG, "NULL pair output arrays");
+    if (maxc > kPairCap)
+        return set_error(RASCAL_E_UNSUPPORTED, "a centre has %d neighbours; the no-allocation entry point sorts at most %d "
+                         "per centre (rascal_neighbours has no such limit)", maxc, kPairCap);
+    k_pairs<true><<<pair_blocks, kPairWarps * 32, 0, stream>>>(N, sys->d_positions, info, binbase, bin_start, sorted_hi,
+                                                               atom_struct, atom_cell, atom_wrap, atom_hi, atom_lo, rc2,
+                                                               nbins_cap, d_offsets, nullptr, d_nbr_j, d_shift,
+                                                               reinterpret_cast<float4*>(d_rij), nullptr, nullptr,
                                                                ctx->d_flags);
     RASCAL_LAUNCH_CHECK("k_pairs<fill>");
     return RASCAL_OK;

@@ -97,6 +97,29 @@ static int scan_impl(const Tin* in, int64_t* out, int64_t n, cudaStream_t stream
     return RASCAL_OK;
 }
 
+// Same scan with a caller-provided buffer for the tile sums (scan_tile_sums_len(n) int64 words); allocates nothing.
+template <typename Tin>
+static int scan_into_impl(const Tin* in, int64_t* out, int64_t n, cudaStream_t stream, int64_t* sums) {
+    const int64_t tiles = div_up(n > 0 ? n : 1, kScanTile);
+    k_scan_tiles<Tin><<<(unsigned)tiles, kScanThreads, 0, stream>>>(in, out, n, sums);
+    RASCAL_LAUNCH_CHECK("k_scan_tiles");
+    k_scan_tile_sums<<<1, kScanThreads, 0, stream>>>(sums, tiles, out + n);
+    RASCAL_LAUNCH_CHECK("k_scan_tile_sums");
+    if (tiles > 1) {
+        k_scan_add<<<(unsigned)tiles, kScanThreads, 0, stream>>>(out, n, sums);
+        RASCAL_LAUNCH_CHECK("k_scan_add");
+    }
+    return RASCAL_OK;
+}
+
+int64_t scan_tile_sums_len(int64_t n) { return div_up(n > 0 ? n : 1, kScanTile) + 1; }
+int scan_exclusive_into(const int* in, int64_t* out, int64_t n, cudaStream_t stream, int64_t* sums) {
+    return scan_into_impl<int>(in, out, n, stream, sums);
+}
+int scan_exclusive_into(const int64_t* in, int64_t* out, int64_t n, cudaStream_t stream, int64_t* sums) {
+    return scan_into_impl<int64_t>(in, out, n, stream, sums);
+}
+
 int scan_exclusive(const int* in, int64_t* out, int64_t n, cudaStream_t stream, Arena& scratch) {
     return scan_impl<int>(in, out, n, stream, scratch);
 }
