@@ -195,6 +195,44 @@ int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d
  * (d_dout may be NULL). Used to build the spline and the MLP training targets. */
 int rascal_radial_exact_fp64(rascal_ctx* ctx, int64_t n_points, const double* d_r, double* d_out, double* d_dout);
 
+/* Switches the radial source of an existing context between RASCAL_RADIAL_SPLINE (table), RASCAL_RADIAL_EXACT
+ * (per pair, 1F1 closed form with the downward recurrence of Appendix A, FP64, then S^-1/2) and RASCAL_RADIAL_MLP
+ * (the context's network). EXACT and MLP compute the per-pair values in a pass before the pair kernels and read
+ * the pair count from the device (one stream synchronisation). */
+int rascal_set_radial(rascal_ctx* ctx, int radial);
+
+/* ---------------- learned radial surrogate: r -> {I^o_nl(r)}, a 1 -> H -> H -> F SiLU network ----------------
+ * Not in the paper (its nearest hook is the remark that the radial basis invites numerical optimisation, end of
+ * Sec. 'Spline optimization'). t = r / r_cut; z1 = W1 t + b1; h1 = silu(z1); z2 = W2 h1 + b2; h2 = silu(z2);
+ * y = W3 h2 + b3; I^o_f(r) ~ scale_f y_f with f = l*n_max + n. Parameters: one FP32 vector
+ * [W1 (H) | b1 (H) | W2 (H x H, row = output) | b2 (H) | W3 (F x H) | b3 (F)]; H must be 64.
+ * Training runs FP32 on the CUDA cores (forward, backward, Adam); inference runs on tcgen05 with BF16 weights and
+ * activations and FP32 accumulation. */
+int rascal_mlp_num_params(const rascal_ctx* ctx, int hidden); /* -1 if hidden is not supported */
+/* Copies host parameters and output scales [F] in, resets the Adam state and packs the BF16 tensor-core tiles. */
+int rascal_mlp_set_params(rascal_ctx* ctx, int hidden, const float* h_params, const float* h_scale);
+int rascal_mlp_get_params(rascal_ctx* ctx, float* h_params, float* h_scale);
+/* Training targets I^o_f(r)/scale_f at n distances d_r (float64, device) into d_targets [n][F] (float32): the exact
+ * FP64 integrals (Eq. rad-int-gto-1, Appendix A) are computed on a grid of dense_intervals (0: 8192) and
+ * interpolated by their clamped FP64 spline (error ~1e-14 at 8192 intervals); h_scale_out [F] (host) receives
+ * scale_f = max over the grid of |I^o_f|. */
+int rascal_mlp_targets(rascal_ctx* ctx, int64_t n, const double* d_r, int dense_intervals, float* d_targets,
+                       float* h_scale_out);
+/* `steps` Adam steps (beta 0.9/0.999, eps 1e-8, cosine learning rate from lr_max to lr_min over total_steps) on
+ * minibatches of `batch` samples taken in the order d_order (int64 indices into the n_samples inputs, drawn by
+ * the caller); d_loss [steps] (optional) receives each step's loss. Repacks the inference tiles at the end. */
+int rascal_mlp_train(rascal_ctx* ctx, int64_t n_samples, const float* d_t, const float* d_targets,
+                     const int64_t* d_order, int batch, int steps, float lr_max, float lr_min, int total_steps,
+                     float* d_loss);
+/* Loss and parameter gradient of one batch (no update): d_grad [n_params], d_loss [1]. */
+int rascal_mlp_gradients(rascal_ctx* ctx, int batch, const float* d_t, const float* d_targets, float* d_grad,
+                         float* d_loss);
+/* Tensor-core inference at n distances d_r (float32): d_out [n][F] = scale_f y_f, d_dout (optional) its r-derivative. */
+int rascal_mlp_eval(rascal_ctx* ctx, int64_t n, const float* d_r, float* d_out, float* d_dout);
+/* Checkpoint: parameters, Adam moments, step count and the hypers they belong to, in a small binary file. */
+int rascal_mlp_save(rascal_ctx* ctx, const char* path);
+int rascal_mlp_load(rascal_ctx* ctx, const char* path);
+
 #ifdef __cplusplus
 }
 #endif

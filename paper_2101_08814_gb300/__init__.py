@@ -201,6 +201,87 @@ class SoapCalculator:
                                                _ptr(forces), _ptr(virial)))
         return forces, virial
 
+    # ---------------------------------------------------------------------------------------- radial source
+    def set_radial(self, mode: str):
+        """'spline' (table), 'exact' (per-pair 1F1 in FP64) or 'mlp' (the trained network)."""
+        _lib.check(_lib.lib().rascal_set_radial(self._ctx, RADIAL[mode]))
+
+    # ---------------------------------------------------------------------------------------- MLP surrogate
+    MLP_HIDDEN = 64
+
+    def mlp_num_params(self):
+        return int(_lib.lib().rascal_mlp_num_params(self._ctx, self.MLP_HIDDEN))
+
+    def mlp_set_params(self, params, scale):
+        import numpy as np
+
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        s = np.ascontiguousarray(scale, dtype=np.float32)
+        if p.size != self.mlp_num_params() or s.size != self.n_max * (self.l_max + 1):
+            raise ValueError("parameter or scale vector of the wrong size")
+        self._bind_stream()
+        _lib.check(_lib.lib().rascal_mlp_set_params(self._ctx, self.MLP_HIDDEN, p.ctypes.data_as(C.c_void_p),
+                                                    s.ctypes.data_as(C.c_void_p)))
+
+    def mlp_get_params(self):
+        import numpy as np
+
+        p = np.empty(self.mlp_num_params(), dtype=np.float32)
+        s = np.empty(self.n_max * (self.l_max + 1), dtype=np.float32)
+        self._bind_stream()
+        _lib.check(_lib.lib().rascal_mlp_get_params(self._ctx, p.ctypes.data_as(C.c_void_p), s.ctypes.data_as(C.c_void_p)))
+        return p, s
+
+    def mlp_targets(self, r, dense_intervals=0):
+        """Scaled FP64-exact targets [n, F] (float32, device) at distances r, and the scales [F] (numpy)."""
+        import numpy as np
+        import torch
+
+        self._bind_stream()
+        r = torch.as_tensor(r, dtype=torch.float64, device=self.device).contiguous()
+        F = self.n_max * (self.l_max + 1)
+        out = torch.empty((r.shape[0], F), dtype=torch.float32, device=self.device)
+        scale = np.empty(F, dtype=np.float32)
+        _lib.check(_lib.lib().rascal_mlp_targets(self._ctx, r.shape[0], _ptr(r), int(dense_intervals), _ptr(out),
+                                                 scale.ctypes.data_as(C.c_void_p)))
+        return out, scale
+
+    def mlp_train(self, t, targets, order, batch, steps, lr_max=3e-3, lr_min=1e-5, total_steps=0, record_loss=True):
+        import torch
+
+        self._bind_stream()
+        loss = torch.zeros(steps, dtype=torch.float32, device=self.device) if record_loss else None
+        _lib.check(_lib.lib().rascal_mlp_train(self._ctx, int(t.shape[0]), _ptr(t), _ptr(targets), _ptr(order), int(batch),
+                                               int(steps), float(lr_max), float(lr_min), int(total_steps), _ptr(loss)))
+        return loss
+
+    def mlp_gradients(self, t, targets):
+        import torch
+
+        self._bind_stream()
+        g = torch.empty(self.mlp_num_params(), dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        _lib.check(_lib.lib().rascal_mlp_gradients(self._ctx, int(t.shape[0]), _ptr(t), _ptr(targets), _ptr(g), _ptr(loss)))
+        return g, loss
+
+    def mlp_eval(self, r, derivative=False):
+        import torch
+
+        self._bind_stream()
+        r = torch.as_tensor(r, dtype=torch.float32, device=self.device).contiguous()
+        F = self.n_max * (self.l_max + 1)
+        out = torch.empty((r.shape[0], F), dtype=torch.float32, device=self.device)
+        dout = torch.empty_like(out) if derivative else None
+        _lib.check(_lib.lib().rascal_mlp_eval(self._ctx, r.shape[0], _ptr(r), _ptr(out), _ptr(dout)))
+        return (out, dout) if derivative else out
+
+    def mlp_save(self, path):
+        _lib.check(_lib.lib().rascal_mlp_save(self._ctx, str(path).encode()))
+
+    def mlp_load(self, path):
+        self._bind_stream()
+        _lib.check(_lib.lib().rascal_mlp_load(self._ctx, str(path).encode()))
+
     def radial_exact_fp64(self, r, derivative=False):
         import torch
 

@@ -97,6 +97,17 @@ _SIGNATURES = {
     "rascal_gradients": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rascal_radial_exact_fp64": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rascal_set_radial": (C.c_int, [C.c_void_p, C.c_int]),
+    "rascal_mlp_num_params": (C.c_int, [C.c_void_p, C.c_int]),
+    "rascal_mlp_set_params": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "rascal_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rascal_mlp_targets": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "rascal_mlp_train": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                   C.c_float, C.c_float, C.c_int, C.c_void_p]),
+    "rascal_mlp_gradients": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rascal_mlp_eval": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rascal_mlp_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "rascal_mlp_load": (C.c_int, [C.c_void_p, C.c_char_p]),
 }
 
 

@@ -112,6 +112,16 @@ struct rascal_ctx {
     int* d_fmap;    // [F_pad] table column (l*n_max + n) of a padded radial slot, -1 for padding
     int* d_pstasks; // power-spectrum tasks, see power_spectrum.cu
     int n_pstasks;
+
+    // MLP surrogate of the radial integrals (mlp.cu); mlp_params == NULL until parameters are set
+    float* mlp_params;   // FP32 master parameters
+    float* mlp_m;        // Adam moments
+    float* mlp_v;
+    float* mlp_grad;
+    float* mlp_scale;    // [F] output scales
+    void* mlp_w2t;       // BF16 operand tiles for the tensor-core inference
+    void* mlp_w3t;
+    int mlp_hidden, mlp_step;
 };
 
 namespace rascal {
@@ -154,7 +164,16 @@ int scan_exclusive_into(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
 
 int validate_system(const rascal_ctx* ctx, const rascal_system* sys);
 
+int radial_grid_fp64(rascal_ctx* ctx, int M, double* grid, double* ends, double* y, double* yend, double* dyend,
+                     double* cp, double* y2);
+// MLP surrogate (mlp.cu): batched inference on the tensor cores; per-pair radial values of the EXACT mode
+int mlp_infer(rascal_ctx* ctx, int64_t n, const float4* rij, const float* r, float* out, float* dout);
+int radial_exact_pairs(rascal_ctx* ctx, int64_t n, const float4* rij, float* out, float* dout);
+int radial_precompute(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const float* d_rij, bool deriv,
+                      const float** pre_G, const float** pre_D);
+
 // per-translation-unit setup called from rascal_create
+int mlp_setup(rascal_ctx* ctx);
 int expansion_setup(rascal_ctx* ctx);
 int power_spectrum_setup(rascal_ctx* ctx);
 int gradients_setup(rascal_ctx* ctx);

@@ -303,6 +303,24 @@ static int launch_radial_fp64(rascal_ctx* ctx, int64_t n_pts, const double* d_r,
     return RASCAL_OK;
 }
 
+// Exact FP64 integrals on the uniform grid r_k = k r_cut/M (y [(M+1)][n_max][L1]), end slopes, and the clamped
+// spline second derivatives (y2 [F][M+1]); used for the MLP training targets.
+int radial_grid_fp64(rascal_ctx* ctx, int M, double* grid, double* ends, double* y, double* yend, double* dyend,
+                     double* cp, double* y2) {
+    const int n_max = ctx->n_max, L1 = ctx->l_max + 1, F = ctx->F;
+    const double delta = ctx->r_cut / M;
+    int st;
+    k_fill_grid<<<div_up(M + 1, 256), 256, 0, ctx->stream>>>(M + 1, delta, 0.0, grid);
+    RASCAL_LAUNCH_CHECK("k_fill_grid");
+    k_fill_grid<<<1, 32, 0, ctx->stream>>>(2, ctx->r_cut, 0.0, ends);
+    RASCAL_LAUNCH_CHECK("k_fill_grid");
+    if ((st = launch_radial_fp64(ctx, M + 1, grid, y, nullptr))) return st;
+    if ((st = launch_radial_fp64(ctx, 2, ends, yend, dyend))) return st;
+    k_spline_solve<<<div_up(F, 64), 64, 0, ctx->stream>>>(M, n_max, L1, delta, y, dyend, cp, y2);
+    RASCAL_LAUNCH_CHECK("k_spline_solve");
+    return RASCAL_OK;
+}
+
 static int build_table(rascal_ctx* ctx, int M, double* errs_host) {
     const int n_max = ctx->n_max, L1 = ctx->l_max + 1, F = ctx->F;
     const double delta = ctx->r_cut / M;
@@ -369,6 +387,13 @@ extern "C" void rascal_destroy(rascal_ctx* ctx) {
     cudaFree(ctx->d_tasks);
     cudaFree(ctx->d_fmap);
     cudaFree(ctx->d_pstasks);
+    cudaFree(ctx->mlp_params);
+    cudaFree(ctx->mlp_m);
+    cudaFree(ctx->mlp_v);
+    cudaFree(ctx->mlp_grad);
+    cudaFree(ctx->mlp_scale);
+    cudaFree(ctx->mlp_w2t);
+    cudaFree(ctx->mlp_w3t);
     cudaFreeHost(ctx->h_flags);
     cudaFreeHost(ctx->h_pinned);
     cudaFree(ctx->scratch.ptr);
@@ -388,8 +413,6 @@ static int create_impl(const rascal_hypers* h, void* stream, rascal_ctx** out) {
         return set_error(RASCAL_E_ARG, "n_species must be in [1, %d] with a species list", kMaxSpecies);
     if (h->n_species * h->n_max > kMaxQ) return set_error(RASCAL_E_ARG, "n_species*n_max must be <= %d", kMaxQ);
     if (h->radial < 0 || h->radial > 2) return set_error(RASCAL_E_ARG, "unknown radial mode %d", h->radial);
-    if (h->radial == RASCAL_RADIAL_EXACT || h->radial == RASCAL_RADIAL_MLP)
-        return set_error(RASCAL_E_UNSUPPORTED, "radial mode %d is not available in this build", h->radial);
     std::vector<int> sp(h->species, h->species + h->n_species);
     std::sort(sp.begin(), sp.end());
     for (int i = 0; i < h->n_species; ++i) {
@@ -458,6 +481,7 @@ static int create_impl(const rascal_hypers* h, void* stream, rascal_ctx** out) {
     if ((st = expansion_setup(ctx))) return st;
     if ((st = power_spectrum_setup(ctx))) return st;
     if ((st = gradients_setup(ctx))) return st;
+    if ((st = mlp_setup(ctx))) return st;
     RASCAL_CUDA(cudaStreamSynchronize(ctx->stream));
     return RASCAL_OK;
 }
@@ -470,6 +494,14 @@ extern "C" int rascal_create(const rascal_hypers* h, void* stream, rascal_ctx** 
         *out = nullptr;
     }
     return st;
+}
+
+extern "C" int rascal_set_radial(rascal_ctx* ctx, int radial) {
+    clear_error();
+    if (!ctx) return set_error(RASCAL_E_ARG, "NULL context");
+    if (radial < RASCAL_RADIAL_SPLINE || radial > RASCAL_RADIAL_MLP) return set_error(RASCAL_E_ARG, "unknown radial mode %d", radial);
+    ctx->radial = radial;
+    return RASCAL_OK;
 }
 
 extern "C" int rascal_set_stream(rascal_ctx* ctx, void* stream) {

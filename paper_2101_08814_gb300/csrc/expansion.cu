@@ -41,6 +41,7 @@ struct ExpArgs {
     const int* species;
     const int* lut;
     const float4* table;
+    const float* pre_G;  // per-pair radial values [P][F] (EXACT / MLP modes) or NULL (spline table)
     const int* tasks;
     const int* fmap;
     float* coeffs;
@@ -217,8 +218,12 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     const int col = s_fmap[fp];
                     float val = 0.0f;
                     if (col >= 0) {
-                        const float4 c = __ldg(&trow[col]);
-                        val = fc * fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
+                        if (A.pre_G) {
+                            val = fc * __ldg(&A.pre_G[(pos + p) * A.F + col]);
+                        } else {
+                            const float4 c = __ldg(&trow[col]);
+                            val = fc * fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
+                        }
                     }
                     grow[fp] = val;
                 }
@@ -590,7 +595,9 @@ extern "C" int rascal_spherical_expansion(rascal_ctx* ctx, const rascal_system* 
     if (st) return st;
     if (sys->n_atoms == 0) return RASCAL_OK;
     if (!d_offsets || !d_nbr_j || !d_rij || !d_coeffs) return set_error(RASCAL_E_ARG, "NULL device pointer");
-    const ExpArgs A = make_args(ctx, sys, d_offsets, d_nbr_j, d_rij, d_coeffs);
+    ExpArgs A = make_args(ctx, sys, d_offsets, d_nbr_j, d_rij, d_coeffs);
+    const float* pre_D;
+    if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, false, &A.pre_G, &pre_D))) return st;
     return launch_expansion<kGramNone>(ctx, A, sys->n_atoms, ctx->plan.threads, ctx->plan.smem);
 }
 
@@ -605,6 +612,8 @@ extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int6
     if (sys->n_atoms == 0) return RASCAL_OK;
     if (!d_offsets || !d_nbr_j || !d_rij || !d_coeffs || !d_ps) return set_error(RASCAL_E_ARG, "NULL device pointer");
     ExpArgs A = make_args(ctx, sys, d_offsets, d_nbr_j, d_rij, d_coeffs);
+    const float* pre_D;
+    if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, false, &A.pre_G, &pre_D))) return st;
     const int mode = precision == RASCAL_PS_FP32 ? kGramSimt : (precision == RASCAL_PS_BF16 ? kGramBf16 : kGramTf32x3);
     size_t smem;
     int threads;

@@ -61,6 +61,8 @@ struct GradArgs {
     const int* lut;
     const int* offs;        // structure offsets
     const float4* table;
+    const float* pre_G;  // per-pair radial values and r-derivatives (EXACT / MLP modes) or NULL
+    const float* pre_D;
     const int* fmap;
     const float* coeffs;
     const float* grad_ps;   // [N][Fp] or NULL
@@ -172,9 +174,14 @@ __global__ void __launch_bounds__(kGradThreads) k_gradients(const GradArgs A) {
                 const int col = s_fmap[fp];
                 float g = 0.0f, dg = 0.0f;
                 if (col >= 0) {
-                    const float4 cf = __ldg(&trow[col]);
-                    g = fmaf(u, fmaf(u, fmaf(u, cf.w, cf.z), cf.y), cf.x);
-                    dg = fmaf(u, fmaf(u, 3.0f * cf.w, 2.0f * cf.z), cf.y) * A.inv_delta;
+                    if (A.pre_G) {
+                        g = __ldg(&A.pre_G[(pos + p) * A.F + col]);
+                        dg = __ldg(&A.pre_D[(pos + p) * A.F + col]);
+                    } else {
+                        const float4 cf = __ldg(&trow[col]);
+                        g = fmaf(u, fmaf(u, fmaf(u, cf.w, cf.z), cf.y), cf.x);
+                        dg = fmaf(u, fmaf(u, 3.0f * cf.w, 2.0f * cf.z), cf.y) * A.inv_delta;
+                    }
                 }
                 s_G[(size_t)p * A.F_pad + fp] = f * g;
                 s_D[(size_t)p * A.F_pad + fp] = df * g + f * dg;
@@ -396,6 +403,7 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
     A.chunk = chunk;
     const size_t smem = grad_smem(ctx, chunk);
     if (smem > 220 * 1024) return set_error(RASCAL_E_UNSUPPORTED, "hypers too large for the gradient kernel");
+    if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, true, &A.pre_G, &A.pre_D))) return st;
     k_gradients<<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A);
     RASCAL_LAUNCH_CHECK("k_gradients");
     return RASCAL_OK;

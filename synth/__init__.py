@@ -14,5 +14,7 @@ from .structures import (  # noqa: F401
     config_mlp,
     CONFIGS,
     linear_weights,
+    mlp_initial_params,
+    mlp_training_draws,
     small_cell_system,
 )

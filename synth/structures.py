@@ -222,6 +222,29 @@ def small_cell_system(seed: int = 11, n_atoms: int = 6, L: float = 4.0, skew: fl
                   hyp, "small-cell")
 
 
+def mlp_initial_params(hidden: int, n_out: int, seed: int = 21) -> np.ndarray:
+    """Seeded initial parameters of the 1 -> H -> H -> F network, flattened as [W1 | b1 | W2 | b2 | W3 | b3].
+
+    W1 ~ N(0, 4) spreads the first-layer kinks over t in [0, 1]; b1 ~ U(-2, 2); W2, W3 ~ N(0, 1/H); biases 0."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W1 = rng.standard_normal(hidden) * 2.0
+    b1 = rng.uniform(-2.0, 2.0, hidden)
+    W2 = rng.standard_normal((hidden, hidden)) / np.sqrt(hidden)
+    W3 = rng.standard_normal((n_out, hidden)) / np.sqrt(hidden)
+    return np.concatenate([W1, b1, W2.ravel(), np.zeros(hidden), W3.ravel(), np.zeros(n_out)]).astype(np.float32)
+
+
+def mlp_training_draws(n_samples: int, r_max: float, batch: int, steps: int, seed: int = 22):
+    """Seeded training distances r ~ U[0, r_max] (both end points included) and the minibatch order: a fresh
+    permutation of the samples per epoch, concatenated to cover `steps` batches."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r = rng.uniform(0.0, r_max, n_samples)
+    r[0], r[1] = 0.0, r_max
+    need = batch * steps
+    order = np.concatenate([rng.permutation(n_samples) for _ in range(max(1, -(-need // n_samples)))])[:max(need, batch)]
+    return r, order.astype(np.int64)
+
+
 def linear_weights(n_species: int, n_features: int, seed: int = 4) -> np.ndarray:
     """Gaussian N(0,1) weights of the additive linear energy model, one row per centre species."""
     rng = np.random.Generator(np.random.PCG64(seed))
