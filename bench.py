@@ -29,6 +29,11 @@ METRIC = "atomic environments/sec (expansion+power spectrum, ±gradients) at sta
 UNIT = "env/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + written) per environment of the fused pair kernel with the FP32 power spectrum
+# (k_expansion<kGramSimt>, PACKED layout) on the batch workload's recipe, from one ncu capture of a 96-cell case:
+# (7.893 MB + 906.711 MB) / 13 434 environments (profiles/k_expansion_fused_fp32_batch96.md). Scaled to a full
+# launch by the environments it processes; valid only while that kernel is unchanged.
+FUSED_FP32_TRAFFIC_PER_ENV = (7.893e6 + 906.711e6) / 13434
 
 WORKLOADS = {
     "batch": "512 periodic cubic cells, 64-216 atoms each (uniform), 0.05 atoms/A^3, 4 species uniform, d_min 1.8 A; "
@@ -317,7 +322,9 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     achieved = (alg / (t_ms * 1e-3) / 1e9) if alg else None
     roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": (FUSED_FP32_TRAFFIC_PER_ENV * N if (fused and args.config == "batch" and args.ps == "fp32"
+                                                               and args.layout == "packed") else None),
                 "algorithmic_bytes_per_launch": alg, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s"}
 
