@@ -65,6 +65,7 @@ struct Arena {
 //   S_c species accumulated concurrently, rounds = ceil(n_species / S_c)
 struct ExpPlan {
     int n_pad, F_pad, Lp;
+    int Ly;           // Y row pitch in the expansion kernel: Lp rounded up so that Ly / 4 is odd (conflict-free rows)
     int lp[kMaxLMax + 2];
     int T_s, W_s, S_c, rounds, threads;
     int chunk;        // pairs staged per chunk

@@ -46,21 +46,23 @@ struct ExpArgs {
     const int* fmap;
     float* coeffs;
     unsigned* flags;
-    int N, n_max, l_max, S, n_lm, F, F_pad, n_pad, Lp, M, T_s, W_s, S_c, rounds, chunk, include_center;
+    int N, n_max, l_max, S, n_lm, F, F_pad, n_pad, Lp, Ly, M, T_s, W_s, S_c, rounds, chunk, include_center;
     float inv_delta, r_cut, width;
     int lp[kMaxLMax + 2];
     // fused power spectrum
     float* ps;
     int64_t ps_stride;
     int layout, ps_norm, Q, per_l;
-    int gram_off;                   // bytes: CT (SIMT) or operand tiles (tensor cores)
+    int gram_off;                   // bytes: CT (SIMT, behind the pair area) or operand tiles (tensor cores, at 0)
+    int pair_off;                   // bytes: start of the pair staging area (behind the tiles in tensor-core mode)
     int stage_floats;               // capacity of the staging area (aliases the pair buffers)
+    int p_half;                     // SIMT: the staging area holds two halves of p_half floats
     int n_groups;
     int g_lo[kMaxGroups], g_hi[kMaxGroups];      // l range [g_lo, g_hi) of each output group
     const int* ps_tasks;            // SIMT tasks, l descending
     int g_tbeg[kMaxGroups], g_tend[kMaxGroups];  // SIMT task ranges of the groups
     int Qp;                         // SIMT CT row pitch
-    int N_mma, tm_cols, lo_off, tiles_bytes;
+    int N_mma, tm_cols, slot_cols, lo_off, tiles_bytes;
     int tile_off[kMaxLMax + 1], sbo[kMaxLMax + 1], nk[kMaxLMax + 1];
 };
 
@@ -70,17 +72,47 @@ __device__ inline float cutoff_fp32(float r, float r_cut, float w) {
     return 0.5f * (1.0f + cospif((r - r_cut + w) / w));
 }
 
+// Position (in floats, 0..3) at which a staged block must start in a 16-byte aligned buffer so that the staged and
+// the global addresses agree modulo 16 bytes.
+__device__ inline int stage_shift(const float* dst) { return (int)((reinterpret_cast<uintptr_t>(dst) >> 2) & 3); }
+
+// Writes count floats staged at st (st and dst congruent mod 16 bytes) to dst: thread 0 issues one bulk copy for
+// the aligned body, threads 0..6 store the ragged head and tail. Call after the fence and barrier that publish st.
+__device__ inline void store_staged(float* dst, const float* st, int count) {
+    const int head = min((4 - stage_shift(dst)) & 3, count);
+    const int body = (count - head) & ~3;
+    const int tail = count - head - body;
+    const int t = threadIdx.x;
+    if (t == 0) {  // one bulk group per call, possibly empty, so that waits can count calls
+        if (body > 0) bulk_store(dst + head, st + head, (uint32_t)body * 4u);
+        bulk_commit();
+    }
+    if (t < head) dst[t] = st[t];
+    if (t >= 4 && t < 4 + tail) dst[head + body + t - 4] = st[head + body + t - 4];
+}
+
+// CTA-wide copy of count floats from shared memory (16-byte aligned) to global memory, by float4 when dst allows
+__device__ inline void copy_out(float* __restrict__ dst, const float* __restrict__ src, int count) {
+    if (((reinterpret_cast<uintptr_t>(dst) & 15) | (count & 3)) == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int t = threadIdx.x; t < (count >> 2); t += blockDim.x) d4[t] = s4[t];
+    } else {
+        for (int t = threadIdx.x; t < count; t += blockDim.x) dst[t] = src[t];
+    }
+}
+
 template <int GRAM>
 __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t s_bar;
+    __shared__ uint64_t s_bar[2];
     __shared__ uint32_t s_tmem;
     constexpr bool TC = (GRAM == kGramBf16 || GRAM == kGramTf32x3);
     const int chunk = A.chunk;
-    float4* s_vec = reinterpret_cast<float4*>(smem_raw);
+    float4* s_vec = reinterpret_cast<float4*>(smem_raw + A.pair_off);
     float* s_G = reinterpret_cast<float*>(s_vec + chunk);            // [chunk][F_pad]
-    float* s_Y = s_G + (size_t)chunk * A.F_pad;                       // [chunk][Lp]
-    float* s_fc = s_Y + (size_t)chunk * A.Lp;
+    float* s_Y = s_G + (size_t)chunk * A.F_pad;                       // [chunk][Ly]
+    float* s_fc = s_Y + (size_t)chunk * A.Ly;
     int* s_spc = reinterpret_cast<int*>(s_fc + chunk);
     int* s_list = s_spc + chunk;
     int* s_start = s_list + chunk;                                    // [kMaxSpecies + 1]
@@ -92,11 +124,15 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
     const int i = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     if (tid < kMaxLMax + 2) s_lp[tid] = A.lp[tid];
+    #pragma unroll 1
     for (int t = tid; t < A.F_pad; t += blockDim.x) s_fmap[t] = A.fmap[t];
-    if (GRAM == kGramSimt) {  // padding columns Q..Qp-1 of CT must read as zero
+    if (GRAM == kGramSimt) {  // columns Q..ceil4(Q)-1 of CT are read by the edge tiles and must be zero
         float* CT = reinterpret_cast<float*>(gram);
-        const int padc = A.Qp - A.Q;
-        for (int e = tid; e < A.n_lm * padc; e += blockDim.x) CT[(e / padc) * A.Qp + A.Q + e % padc] = 0.0f;
+        const int q_end = (A.Q + 3) & ~3;
+        if (q_end > A.Q)
+            for (int lm = tid; lm < A.n_lm; lm += blockDim.x)
+                #pragma unroll 1
+                for (int c = A.Q; c < q_end; ++c) CT[lm * A.Qp + c] = 0.0f;
     }
     if (TC) {  // K padding and rows >= Q of the operand tiles must read as zero
         for (int b = tid; b < A.tiles_bytes / 16; b += blockDim.x)
@@ -106,7 +142,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
             tmem_relinquish();
         }
         if (tid == 0) {
-            mbar_init(&s_bar, 1);
+            mbar_init(&s_bar[0], 1);
+            mbar_init(&s_bar[1], 1);
             fence_mbar_init();
         }
         tc_fence_before();
@@ -140,6 +177,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
 
         for (int64_t pos = seg_beg; pos < seg_end; pos += chunk) {
             const int nc = (int)((seg_end - pos) < (int64_t)chunk ? (seg_end - pos) : (int64_t)chunk);
+            #pragma unroll 1
             for (int t = tid; t < nc; t += blockDim.x) {
                 const float4 v = A.rij[pos + t];
                 const int j = A.nbr_j[pos + t];
@@ -154,9 +192,11 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
             __syncthreads();
             if (warp == 0) {
                 int base = 0;
+                #pragma unroll 1
                 for (int ga = 0; ga < na; ++ga) {
                     const int a = a0 + ga;
                     if (lane == 0) s_start[ga] = base;
+                    #pragma unroll 1
                     for (int p0 = 0; p0 < nc; p0 += 32) {
                         const int p = p0 + lane;
                         const bool mine = (p < nc) && (s_spc[p] == a);
@@ -169,77 +209,98 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
             }
             __syncthreads();
             const int n_list = s_start[na];
-            // Y_lm: one thread per (listed pair, m) chain
-            for (int idx = tid; idx < n_list * L1; idx += blockDim.x) {
-                const int q = idx / L1;
-                const int m = idx - q * L1;
-                const float4 v = s_vec[s_list[q]];
-                const float inv_r = 1.0f / v.w;
-                const float x = v.x * inv_r, y = v.y * inv_r, z = v.z * inv_r;
-                float cm = 1.0f, sm = 0.0f;
-                for (int t = 0; t < m; ++t) {
-                    const float nc2 = cm * x - sm * y;
-                    sm = cm * y + sm * x;
-                    cm = nc2;
-                }
-                float* yrow = s_Y + (size_t)q * A.Lp;
-                float q2 = 0.0f, q1 = c_ylm_K[m];
-                if (m == 0) {
-                    yrow[s_lp[0]] = q1;
-                } else {
-                    yrow[s_lp[m] + 2 * m] = q1 * cm;
-                    yrow[s_lp[m]] = q1 * sm;
-                }
-                for (int l = m + 1; l <= A.l_max; ++l) {
-                    const float qq = c_ylm_A[l * 16 + m] * (z * q1 - c_ylm_B[l * 16 + m] * q2);
-                    if (m == 0) {
-                        yrow[s_lp[l] + l] = qq;
-                    } else {
-                        yrow[s_lp[l] + l + m] = qq * cm;
-                        yrow[s_lp[l] + l - m] = qq * sm;
+            // Y_lm: warp w runs the chains of m = w, w + nwarps, ... with the lanes over the listed pairs, so the
+            // recurrence coefficients and the loop bounds are uniform across the warp
+            #pragma unroll 1
+            for (int m = warp; m < L1; m += nwarps) {
+                const float km = c_ylm_K[m];
+                #pragma unroll 1
+                for (int q = lane; q < n_list; q += 32) {
+                    const float4 v = s_vec[s_list[q]];
+                    const float inv_r = 1.0f / v.w;
+                    const float x = v.x * inv_r, y = v.y * inv_r, z = v.z * inv_r;
+                    float cm = 1.0f, sm = 0.0f;
+                    #pragma unroll 1
+                    for (int t = 0; t < m; ++t) {
+                        const float nc2 = cm * x - sm * y;
+                        sm = cm * y + sm * x;
+                        cm = nc2;
                     }
-                    q2 = q1;
-                    q1 = qq;
-                }
-            }
-            // radial values G = f_cut I^o_nl from the spline: one warp per listed pair, lanes over padded (l, n)
-            for (int q = warp; q < n_list; q += nwarps) {
-                const int p = s_list[q];
-                const float r = s_vec[p].w;
-                const float fc = s_fc[p];
-                const float x = r * A.inv_delta;
-                int k = (int)x;
-                k = min(max(k, 0), A.M - 1);
-                const float u = x - (float)k;
-                const float4* trow = A.table + (int64_t)k * A.F;
-                float* grow = s_G + (size_t)q * A.F_pad;
-#pragma unroll 4
-                for (int fp = lane; fp < A.F_pad; fp += 32) {
-                    const int col = s_fmap[fp];
-                    float val = 0.0f;
-                    if (col >= 0) {
-                        if (A.pre_G) {
-                            val = fc * __ldg(&A.pre_G[(pos + p) * A.F + col]);
-                        } else {
-                            const float4 c = __ldg(&trow[col]);
-                            val = fc * fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
+                    float* yrow = s_Y + q * A.Ly;
+                    float q2 = 0.0f, q1 = km;
+                    if (m == 0) {
+                        yrow[s_lp[0]] = q1;
+                        #pragma unroll 1
+                        for (int l = 1; l < L1; ++l) {
+                            const float qq = c_ylm_A[l * 16] * (z * q1 - c_ylm_B[l * 16] * q2);
+                            yrow[s_lp[l] + l] = qq;
+                            q2 = q1;
+                            q1 = qq;
+                        }
+                    } else {
+                        yrow[s_lp[m] + 2 * m] = q1 * cm;
+                        yrow[s_lp[m]] = q1 * sm;
+                        #pragma unroll 1
+                        for (int l = m + 1; l < L1; ++l) {
+                            const float qq = c_ylm_A[l * 16 + m] * (z * q1 - c_ylm_B[l * 16 + m] * q2);
+                            float* yl = yrow + s_lp[l] + l;
+                            yl[m] = qq * cm;
+                            yl[-m] = qq * sm;
+                            q2 = q1;
+                            q1 = qq;
                         }
                     }
-                    grow[fp] = val;
+                }
+            }
+            // radial values G = f_cut I^o_nl: one warp per listed pair, lanes over padded (l, n); the warps without a
+            // Y chain take the first pairs
+            for (int q = nwarps - 1 - warp; q < n_list; q += nwarps) {
+                const int p = s_list[q];
+                const float fc = s_fc[p];
+                float* grow = s_G + q * A.F_pad;
+                if (A.pre_G) {  // per-pair values (EXACT / MLP radial modes)
+                    const float* prow = A.pre_G + (pos + p) * A.F;
+                    for (int fp = lane; fp < A.F_pad; fp += 32) {
+                        const int col = s_fmap[fp];
+                        grow[fp] = col >= 0 ? fc * __ldg(prow + col) : 0.0f;
+                    }
+                } else {        // cubic spline: interval k, local coordinate u in [0, 1)
+                    const float x = s_vec[p].w * A.inv_delta;
+                    const int k = min(max((int)x, 0), A.M - 1);
+                    const float u = x - (float)k;
+                    const float4* trow = A.table + k * A.F;
+                    for (int fp = lane; fp < A.F_pad; fp += 32) {
+                        const int col = s_fmap[fp];
+                        const float4 c = col >= 0 ? __ldg(trow + col) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        grow[fp] = fc * fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
+                    }
                 }
             }
             __syncthreads();
             if (active) {
                 const int beg = s_start[g], end = s_start[g + 1];
+                uint64_t ap[4][2];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ap[u][0] = f2_pack(acc[u][0], acc[u][1]);
+                    ap[u][1] = f2_pack(acc[u][2], acc[u][3]);
+                }
                 for (int q = beg; q < end; ++q) {
-                    const float4 gv = *reinterpret_cast<const float4*>(s_G + (size_t)q * A.F_pad + g_off);
-                    const float4 yv = *reinterpret_cast<const float4*>(s_Y + (size_t)q * A.Lp + y_off);
+                    const float4 gv = *reinterpret_cast<const float4*>(s_G + q * A.F_pad + g_off);
+                    const float4 yv = *reinterpret_cast<const float4*>(s_Y + q * A.Ly + y_off);
+                    const uint64_t y01 = f2_pack(yv.x, yv.y), y23 = f2_pack(yv.z, yv.w);
                     const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
-                    const float yy[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
+                    for (int u = 0; u < 4; ++u) {
+                        const uint64_t gu = f2_pack(gg[u], gg[u]);
+                        ap[u][0] = f2_fma(gu, y01, ap[u][0]);
+                        ap[u][1] = f2_fma(gu, y23, ap[u][1]);
+                    }
+                }
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(gg[u], yy[v], acc[u][v]);
+                for (int u = 0; u < 4; ++u) {
+                    f2_unpack(ap[u][0], acc[u][0], acc[u][1]);
+                    f2_unpack(ap[u][1], acc[u][2], acc[u][3]);
                 }
             }
             __syncthreads();
@@ -258,6 +319,24 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     }
                 }
             }
+            if (GRAM == kGramSimt) {  // tile -> CT[l^2 + s][a n_max + n]; c reaches HBM from CT afterwards
+                float* ct = reinterpret_cast<float*>(gram) + (my_l * my_l + 4 * my_mt) * A.Qp + a * A.n_max + 4 * my_nt;
+                const int v_end = 2 * my_l + 1 - 4 * my_mt, u_end = A.n_max - 4 * my_nt;
+                const bool vec = u_end >= 4 && (A.n_max & 3) == 0;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    if (v >= v_end) break;
+                    float* row = ct + v * A.Qp;
+                    if (vec) {
+                        *reinterpret_cast<float4*>(row) = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (u < u_end) row[u] = acc[u][v];
+                    }
+                }
+                continue;
+            }
             float* out = A.coeffs + ((int64_t)i * A.S + a) * A.n_max * A.n_lm + my_l * my_l;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -269,10 +348,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     const int s = 4 * my_mt + v;
                     if (s > 2 * my_l) continue;
                     const float cv = acc[u][v];
-                    out[(int64_t)n * A.n_lm + s] = cv;
-                    if (GRAM == kGramSimt) {
-                        reinterpret_cast<float*>(gram)[(my_l * my_l + s) * A.Qp + q] = cv;
-                    } else if (TC) {
+                    out[n * A.n_lm + s] = cv;
+                    if (TC) {
                         constexpr int esz = (GRAM == kGramTf32x3) ? 4 : 2, e16 = 16 / esz;
                         const int off = A.tile_off[my_l] + (q >> 3) * A.sbo[my_l] + (s / e16) * 128 + (q & 7) * 16 + (s % e16) * esz;
                         if (GRAM == kGramTf32x3) {
@@ -292,27 +369,57 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
     // ------------------------------------------------------------------------------------ fused power spectrum
     float* pout = A.ps + (int64_t)i * A.ps_stride;
     if (GRAM == kGramSimt) {
+        fence_proxy_async_smem();
         __syncthreads();
         const float* CT = reinterpret_cast<const float*>(gram);
+        {   // c[q][lm] = CT[lm][q]: lanes over lm (coalesced stores), float4 reads along q
+            float* cdst = A.coeffs + (int64_t)i * A.Q * A.n_lm;
+            const int n_lm = A.n_lm, Qp = A.Qp;
+            for (int q = 4 * warp; q < A.Q; q += 4 * nwarps) {
+                const int nq = A.Q - q;
+                float* d = cdst + q * n_lm + lane;
+                const float* src = CT + lane * Qp + q;
+#pragma unroll 1
+                for (int lm = lane; lm < n_lm; lm += 32, d += 32, src += 32 * Qp) {
+                    const float4 v = *reinterpret_cast<const float4*>(src);
+                    d[0] = v.x;
+                    if (nq > 1) d[n_lm] = v.y;
+                    if (nq > 2) d[2 * n_lm] = v.z;
+                    if (nq > 3) d[3 * n_lm] = v.w;
+                }
+            }
+        }
+        // groups of l alternate between two staging halves; each half is written again only after the bulk store
+        // issued from it two groups earlier has finished reading it
         for (int gi = 0; gi < A.n_groups; ++gi) {
             const int lo = A.g_lo[gi];
+            float* dst = pout + (int64_t)lo * A.per_l;
+            float* st = stage + (gi & 1) * A.p_half + stage_shift(dst);
+            if (gi >= 2) {
+                if (tid == 0) bulk_wait_read<1>();
+                __syncthreads();
+            }
             for (int t = A.g_tbeg[gi] + tid; t < A.g_tend[gi]; t += blockDim.x) {
                 const int packed = __ldg(&A.ps_tasks[t]);
                 const int l = packed & 0xff, t1 = (packed >> 8) & 0xff, t2 = (packed >> 16) & 0xff;
                 float acc[4][4];
                 gram_tile_fp32(CT, A.Qp, l, t1, t2, acc);
-                store_tile_fp32(stage + (size_t)(l - lo) * A.per_l, A.Q, A.layout, t1, t2,
+                store_tile_fp32(st + (l - lo) * A.per_l, A.Q, A.layout, t1, t2,
                                 A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f, acc);
             }
+            fence_proxy_async_smem();
             __syncthreads();
-            float* dst = pout + (int64_t)lo * A.per_l;
-            const int count = (A.g_hi[gi] - lo) * A.per_l;
-            for (int t = tid; t < count; t += blockDim.x) dst[t] = stage[t];
-            __syncthreads();
+            store_staged(dst, st, (A.g_hi[gi] - lo) * A.per_l);
         }
+        if (tid == 0) bulk_wait_all();
         return;
     }
     if (TC) {
+        // One MMA batch per l, D_l = C_l C_l^T (rows 0..Q-1 of a 128-row MMA; rows >= Q read whatever follows the
+        // operand tile and are never used) into one of two TMEM slots: the batch for l + 2 is issued as soon as
+        // the epilogue of l has read its slot, so MMA and epilogue overlap. The epilogue runs on the warps whose
+        // TMEM lane quadrant holds rows < Q, one 16-column chunk per warp, into staging halves that leave by bulk
+        // copies, alternating between groups of l.
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -320,70 +427,79 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         const uint32_t taddr = s_tmem;
         const uint32_t tiles_s = smem_u32(gram);
         const uint32_t idesc = instr_desc(GRAM == kGramTf32x3 ? 2u : 1u, 128u, (uint32_t)A.N_mma);
-        uint32_t phase = 0;
-        bool ok = true;
-        for (int gi = 0; gi < A.n_groups && ok; ++gi) {
-            const int l0 = A.g_lo[gi], l1 = A.g_hi[gi];
-            if (tid == 0) {
-                tc_fence_after();
-                for (int l = l0; l < l1; ++l) {
-                    const uint32_t d = taddr + (uint32_t)((l - l0) * A.N_mma);
-                    for (int kk = 0; kk < A.nk[l]; ++kk) {
-                        const uint32_t a_addr = tiles_s + A.tile_off[l] + kk * 256;
-                        const uint64_t da = smem_desc(a_addr, 128, A.sbo[l]);
-                        if (GRAM == kGramTf32x3) {
-                            const uint64_t dl = smem_desc(a_addr + A.lo_off, 128, A.sbo[l]);
-                            mma_tf32_ss(d, da, da, idesc, kk > 0);
-                            mma_tf32_ss(d, da, dl, idesc, 1);
-                            mma_tf32_ss(d, dl, da, idesc, 1);
-                        } else {
-                            mma_bf16_ss(d, da, da, idesc, kk > 0);
-                        }
-                    }
-                }
-                mma_commit(&s_bar);
-            }
-            const bool done = mbar_wait_bounded(&s_bar, phase);
-            ok = __syncthreads_and(done) != 0;
-            if (!ok) {
-                if (tid == 0) atomicOr(A.flags, kFlagTimeout);
-                mbar_wait_bounded(&s_bar, phase);
-            }
-            phase ^= 1u;
-            tc_fence_after();
-            if (ok && warp < 4) {
-                const int q = 32 * warp + lane;
-                for (int l = l0; l < l1; ++l) {
-                    const float kl = A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f;
-                    float* st = stage + (size_t)(l - l0) * A.per_l;
-                    for (int jb = 0; jb < A.N_mma / 16; ++jb) {
-                        float v[16];
-                        tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)((l - l0) * A.N_mma + 16 * jb), v);
-                        if (q < A.Q) {
-#pragma unroll
-                            for (int t = 0; t < 16; ++t) {
-                                const int q2 = 16 * jb + t;
-                                if (q2 < A.Q) {
-                                    if (A.layout == RASCAL_LAYOUT_PACKED) {
-                                        if (q2 >= q) st[packed_index(q, q2, A.Q)] = kl * v[t];
-                                    } else {
-                                        st[q * A.Q + q2] = kl * v[t];
-                                    }
-                                }
-                            }
-                        }
-                    }
+        const int L1n = A.l_max + 1;
+        auto issue = [&](int l) {
+            const uint32_t d = taddr + (uint32_t)((l & 1) * A.slot_cols);
+            for (int kk = 0; kk < A.nk[l]; ++kk) {
+                const uint32_t a_addr = tiles_s + A.tile_off[l] + kk * 256;
+                const uint64_t da = smem_desc(a_addr, 128, A.sbo[l]);
+                if (GRAM == kGramTf32x3) {
+                    const uint64_t dl = smem_desc(a_addr + A.lo_off, 128, A.sbo[l]);
+                    mma_tf32_ss(d, da, da, idesc, kk > 0);
+                    mma_tf32_ss(d, da, dl, idesc, 1);
+                    mma_tf32_ss(d, dl, da, idesc, 1);
+                } else {
+                    mma_bf16_ss(d, da, da, idesc, kk > 0);
                 }
             }
-            tc_fence_before();
-            __syncthreads();
-            if (ok) {
-                float* dst = pout + (int64_t)l0 * A.per_l;
-                const int count = (l1 - l0) * A.per_l;
-                for (int t = tid; t < count; t += blockDim.x) dst[t] = stage[t];
-            }
-            __syncthreads();
+            mma_commit(&s_bar[l & 1]);
+        };
+        if (tid == 0) {
+            issue(0);
+            if (L1n > 1) issue(1);
         }
+        const int quad = warp & 3, q1 = 32 * quad + lane;
+        const int n_chunks = A.N_mma / 16;
+        const bool packed = A.layout == RASCAL_LAYOUT_PACKED;
+        // offset of row q1 inside an l block: packed rows hold q2 >= q1 at q1 (2Q - q1 - 1) / 2 + q2
+        const int row_off = packed ? (q1 * (2 * A.Q - q1 - 1)) / 2 : q1 * A.Q;
+        bool ok = true;
+        int gi = 0;
+        for (int l = 0; l < L1n; ++l) {
+            const int lo = A.g_lo[gi];
+            float* dst = pout + (int64_t)lo * A.per_l;
+            float* st = stage + (gi & 1) * A.p_half + stage_shift(dst);
+            // warp-uniform, since tcgen05.ld is issued by whole warps
+            const bool done = __all_sync(0xffffffffu, mbar_wait_bounded(&s_bar[l & 1], (uint32_t)((l >> 1) & 1)));
+            tc_fence_after();
+            if (done && 32 * quad < A.Q) {
+                const float kl = A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f;
+                float* row = st + (l - lo) * A.per_l + row_off;
+                const uint32_t tl = taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)((l & 1) * A.slot_cols);
+                for (int jb = warp >> 2; jb < n_chunks; jb += nwarps >> 2) {
+                    if (packed && 16 * jb + 15 < 32 * quad) continue;  // chunk entirely below the diagonal
+                    float v[16];
+                    tmem_ld16(tl + 16 * jb, v);
+                    if (q1 < A.Q) {
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {
+                            const int q2 = 16 * jb + t;
+                            if (q2 < A.Q && (!packed || q2 >= q1)) row[q2] = kl * v[t];
+                        }
+                    }
+                }
+            }
+            const bool group_end = l + 1 == A.g_hi[gi];
+            if (group_end) fence_proxy_async_smem();
+            tc_fence_before();
+            ok = __syncthreads_and(done) != 0;
+            if (!ok) break;
+            tc_fence_after();
+            if (tid == 0 && l + 2 < L1n) issue(l + 2);
+            if (group_end) {
+                store_staged(dst, st, (A.g_hi[gi] - lo) * A.per_l);
+                ++gi;
+                if (gi >= 2 && gi < A.n_groups) {  // the half of group gi was last read by the store of gi - 2
+                    if (tid == 0) bulk_wait_read<1>();
+                    __syncthreads();
+                }
+            }
+        }
+        if (!ok) {  // an MMA batch did not complete in time: flag it and give the outstanding ones another bound
+            if (tid == 0) atomicOr(A.flags, kFlagTimeout);
+            for (int sl = 0; sl < 2; ++sl) mbar_wait_bounded(&s_bar[sl], 0u);
+        }
+        if (tid == 0) bulk_wait_all();
         tc_fence_before();
         __syncthreads();
         if (warp == 0) {
@@ -405,6 +521,7 @@ static void make_plan(rascal_ctx* ctx) {
     }
     for (int l = ctx->l_max + 1; l < kMaxLMax + 2; ++l) P.lp[l] = acc;
     P.Lp = acc;
+    P.Ly = (acc / 4 | 1) * 4;
     int mt_total = 0;
     for (int l = 0; l <= ctx->l_max; ++l) mt_total += (2 * l + 1 + 3) / 4;
     P.T_s = (P.n_pad / 4) * mt_total;
@@ -415,7 +532,7 @@ static void make_plan(rascal_ctx* ctx) {
     P.rounds = (ctx->n_species + P.S_c - 1) / P.S_c;
     P.threads = 32 * P.W_s * P.S_c;
     auto smem_for = [&](int chunk) {
-        return (size_t)chunk * sizeof(float4) + (size_t)chunk * (P.F_pad + P.Lp) * sizeof(float) +
+        return (size_t)chunk * sizeof(float4) + (size_t)chunk * (P.F_pad + P.Ly) * sizeof(float) +
                (size_t)chunk * (sizeof(float) + 2 * sizeof(int)) + (kMaxSpecies + 1 + kMaxLMax + 2 + P.F_pad) * sizeof(int) + 64;
     };
     P.chunk = 32;  // about 30 KB for n_max 12, l_max 9: four CTAs per SM
@@ -477,6 +594,7 @@ static ExpArgs make_args(rascal_ctx* ctx, const rascal_system* sys, const int64_
     A.F_pad = P.F_pad;
     A.n_pad = P.n_pad;
     A.Lp = P.Lp;
+    A.Ly = P.Ly;
     A.M = ctx->M;
     A.T_s = P.T_s;
     A.W_s = P.W_s;
@@ -502,19 +620,25 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
     A.Q = Q;
     A.per_l = layout == RASCAL_LAYOUT_PACKED ? Q * (Q + 1) / 2 : Q * Q;
     A.ps_stride = (int64_t)(ctx->l_max + 1) * A.per_l;
-    const size_t pair_region = (size_t)P.chunk * (P.F_pad + P.Lp);  // floats available for staging
+    const size_t pair_region = (size_t)P.chunk * (P.F_pad + P.Ly);  // floats available for staging
     const int L1 = ctx->l_max + 1;
     *threads = P.threads;
     size_t gram_bytes = 0;
     size_t stage_need = 0;
+    size_t tail_end = 0;  // tensor cores: end of the bytes the last MMA reads
     if (mode == kGramSimt) {
-        A.Qp = (Q + 3) / 4 * 4;
+        // row pitch: a multiple of 4 floats with Qp / 4 odd, so float4 reads down a column of CT are conflict-free
+        A.Qp = ((Q + 3) / 4 | 1) * 4;
         gram_bytes = sizeof(float) * (size_t)ctx->n_lm * A.Qp;
         A.ps_tasks = ctx->d_pstasks;
-        // groups of consecutive l (descending, the task order) whose blocks fit the staging area
-        const int Q4 = A.Qp / 4;
+        // staging: two halves for the p groups; a staged block may start up to 3 floats late (alignment with
+        // its target in global memory)
+        size_t half = std::max((pair_region / 2) / 4 * 4, ((size_t)A.per_l + 3 + 3) / 4 * 4);
+        A.p_half = (int)half;
+        // groups of consecutive l (descending, the task order) whose blocks fit one half
+        const int Q4 = (Q + 3) / 4;
         const int per_tile_l = Q4 * (Q4 + 1) / 2;
-        const size_t cap = std::max(pair_region, (size_t)A.per_l);
+        const size_t cap = half - 3;
         int g = 0, t = 0, l = ctx->l_max;
         while (l >= 0) {
             int n = 0;
@@ -524,45 +648,51 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
             A.g_tbeg[g] = t;
             t += n * per_tile_l;
             A.g_tend[g] = t;
-            stage_need = std::max(stage_need, (size_t)n * A.per_l);
             l -= n;
             ++g;
         }
         A.n_groups = g;
+        stage_need = 2 * half;
     } else {
         if (Q > 128) return set_error(RASCAL_E_UNSUPPORTED, "tensor-core power spectrum needs n_species*n_max <= 128");
         const bool tf32 = mode == kGramTf32x3;
         const int esz = tf32 ? 4 : 2, kstep = tf32 ? 8 : 16, e16 = 16 / esz;
         A.N_mma = (Q + 15) / 16 * 16;
         const int Qr = (Q + 7) / 8 * 8;
-        int off = 0, need = 0;
+        int off = 0, read_end = 0;
         for (int l = 0; l <= ctx->l_max; ++l) {
             const int kpad = (2 * l + 1 + kstep - 1) / kstep * kstep;
             A.nk[l] = kpad / kstep;
             A.sbo[l] = (kpad / e16) * 128;
             A.tile_off[l] = off;
-            need = std::max(need, off + 16 * A.sbo[l]);  // M = 128 rows read from the tile's start
+            read_end = std::max(read_end, off + 16 * A.sbo[l]);  // an M = 128 MMA reads 16 row groups
             off += (Qr / 8) * A.sbo[l];
         }
-        const int hi_bytes = (std::max(off, need) + 1023) / 1024 * 1024;
+        const int hi_bytes = (off + 1023) / 1024 * 1024;
         A.lo_off = tf32 ? hi_bytes : 0;
         A.tiles_bytes = tf32 ? 2 * hi_bytes : hi_bytes;
-        gram_bytes = (size_t)A.tiles_bytes;
-        A.tm_cols = A.N_mma <= 64 ? 128 : 256;
-        const int per_group = A.tm_cols / A.N_mma;
-        const size_t cap = std::max(pair_region, (size_t)A.per_l);
+        // the tiles sit at the start of shared memory and the pair area follows them, so the rows >= Q that the
+        // MMA reads past the last tile stay inside the allocation
+        A.gram_off = 0;
+        A.pair_off = A.tiles_bytes;
+        tail_end = (size_t)A.lo_off + read_end;
+        A.slot_cols = A.N_mma <= 64 ? 64 : 128;
+        A.tm_cols = 2 * A.slot_cols;
+        size_t half = std::max((pair_region / 2) / 4 * 4, ((size_t)A.per_l + 3 + 3) / 4 * 4);
+        A.p_half = (int)half;
+        const size_t cap = half - 3;
         int g = 0;
         for (int l = 0; l < L1;) {
             int n = 0;
-            while (l + n < L1 && n < per_group && (size_t)(n + 1) * A.per_l <= cap) ++n;
+            while (l + n < L1 && (size_t)(n + 1) * A.per_l <= cap) ++n;
             A.g_lo[g] = l;
             A.g_hi[g] = l + n;
-            stage_need = std::max(stage_need, (size_t)n * A.per_l);
             l += n;
             ++g;
         }
         A.n_groups = g;
-        *threads = std::max(*threads, 128);  // the epilogue reads TMEM lanes 0..127 with warps 0..3
+        stage_need = 2 * half;
+        *threads = std::max(*threads, 128);  // the epilogue needs all four TMEM lane quadrants
     }
     // the staging area aliases the pair buffers; grow the pair region if one group needs more
     size_t exp_bytes = P.smem;
@@ -570,8 +700,13 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
     if (stage_need * sizeof(float) > stage_bytes_avail) exp_bytes += stage_need * sizeof(float) - stage_bytes_avail;
     A.stage_floats = (int)std::max(stage_need, pair_region);
     // the staging may run over the (then unused) small arrays behind the pair buffers, up to the gram region
-    A.gram_off = (int)align_up(exp_bytes, 1024);
-    *smem = (size_t)A.gram_off + gram_bytes;
+    if (mode == kGramSimt) {
+        A.pair_off = 0;
+        A.gram_off = (int)align_up(exp_bytes, 1024);
+        *smem = (size_t)A.gram_off + gram_bytes;
+    } else {
+        *smem = std::max((size_t)A.pair_off + exp_bytes, tail_end);
+    }
     if (*smem > 220 * 1024) return set_error(RASCAL_E_UNSUPPORTED, "fused power spectrum needs %zu bytes of shared memory", *smem);
     return RASCAL_OK;
 }

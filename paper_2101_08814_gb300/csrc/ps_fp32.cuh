@@ -6,6 +6,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "f32x2.cuh"
 
 namespace rascal {
 
@@ -13,20 +14,29 @@ __device__ __host__ inline int64_t packed_index(int q1, int q2, int Q) {  // q1 
     return (int64_t)q1 * Q - (int64_t)q1 * (q1 - 1) / 2 + (q2 - q1);
 }
 
+// accumulates the tile with paired FMAs (fma.rn.f32x2): each product is rounded exactly as fmaf rounds it
 __device__ inline void gram_tile_fp32(const float* __restrict__ CT, int Qp, int l, int t1, int t2, float (&acc)[4][4]) {
+    const float* row = CT + l * l * Qp;
+    uint64_t ap[4][2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
-    const float* row = CT + (size_t)(l * l) * Qp;
+    for (int u = 0; u < 4; ++u) ap[u][0] = ap[u][1] = 0ull;
+#pragma unroll 2
     for (int s = 0; s <= 2 * l; ++s, row += Qp) {
         const float4 a = *reinterpret_cast<const float4*>(row + 4 * t1);
         const float4 b = *reinterpret_cast<const float4*>(row + 4 * t2);
-        const float aa[4] = {a.x, a.y, a.z, a.w}, bb[4] = {b.x, b.y, b.z, b.w};
+        const uint64_t b01 = f2_pack(b.x, b.y), b23 = f2_pack(b.z, b.w);
+        const float aa[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t au = f2_pack(aa[u], aa[u]);
+            ap[u][0] = f2_fma(au, b01, ap[u][0]);
+            ap[u][1] = f2_fma(au, b23, ap[u][1]);
+        }
+    }
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(aa[u], bb[v], acc[u][v]);
+    for (int u = 0; u < 4; ++u) {
+        f2_unpack(ap[u][0], acc[u][0], acc[u][1]);
+        f2_unpack(ap[u][1], acc[u][2], acc[u][3]);
     }
 }
 
@@ -37,10 +47,12 @@ __device__ inline void store_tile_fp32(float* __restrict__ o, int Q, int layout,
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int q1 = 4 * t1 + u;
+            // entry (q1, q2) of the packed block sits at q1 (2Q - q1 - 1) / 2 + q2
+            float* row = o + (q1 * (2 * Q - q1 - 1)) / 2 + 4 * t2;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const int q2 = 4 * t2 + v;
-                if (q1 <= q2 && q2 < Q) o[packed_index(q1, q2, Q)] = k * acc[u][v];
+                if (q1 <= q2 && q2 < Q) row[v] = k * acc[u][v];
             }
         }
     } else {

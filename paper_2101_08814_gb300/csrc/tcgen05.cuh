@@ -100,4 +100,20 @@ __device__ inline void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 __device__ inline void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Bulk (non-tensor) asynchronous copy shared -> global by the issuing thread: both addresses 16-byte aligned,
+// size a multiple of 16 bytes. The writers of the source make their stores visible to the async proxy
+// (fence_proxy_async_smem) before the barrier that precedes the issue. Completion is tracked per thread in bulk
+// groups: wait_read<N> returns once at most N committed groups still read shared memory.
+__device__ inline void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 }  // namespace rascal
