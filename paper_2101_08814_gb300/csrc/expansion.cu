@@ -399,7 +399,12 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 if (tid == 0) bulk_wait_read<1>();
                 __syncthreads();
             }
-            for (int t = A.g_tbeg[gi] + tid; t < A.g_tend[gi]; t += blockDim.x) {
+            // tasks are sorted by decreasing cost (l); alternate rounds are dealt in reverse thread order so that
+            // the threads with the longest first tile get the shortest second one
+            const int T = blockDim.x;
+            for (int r = 0; A.g_tbeg[gi] + r * T < A.g_tend[gi]; ++r) {
+                const int t = A.g_tbeg[gi] + r * T + ((r & 1) ? T - 1 - tid : tid);
+                if (t >= A.g_tend[gi]) continue;
                 const int packed = __ldg(&A.ps_tasks[t]);
                 const int l = packed & 0xff, t1 = (packed >> 8) & 0xff, t2 = (packed >> 16) & 0xff;
                 float acc[4][4];
@@ -631,9 +636,10 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
         A.Qp = ((Q + 3) / 4 | 1) * 4;
         gram_bytes = sizeof(float) * (size_t)ctx->n_lm * A.Qp;
         A.ps_tasks = ctx->d_pstasks;
-        // staging: two halves for the p groups; a staged block may start up to 3 floats late (alignment with
-        // its target in global memory)
-        size_t half = std::max((pair_region / 2) / 4 * 4, ((size_t)A.per_l + 3 + 3) / 4 * 4);
+        // staging: two halves that alternate between groups of l, so that the bulk store of one group overlaps
+        // the tiles of the next; a staged block may start up to 3 floats late (alignment with its target in
+        // global memory). (Staging the whole centre at once needs three CTAs per SM and measured slower.)
+        const size_t half = std::max((pair_region / 2) / 4 * 4, ((size_t)A.per_l + 3 + 3) / 4 * 4);
         A.p_half = (int)half;
         // groups of consecutive l (descending, the task order) whose blocks fit one half
         const int Q4 = (Q + 3) / 4;
