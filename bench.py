@@ -31,9 +31,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + written) per environment of the fused pair kernel with the FP32 power spectrum
 # (k_expansion<kGramSimt>, PACKED layout) on the batch workload's recipe, from one ncu capture of a 96-cell case:
-# (7.893 MB + 906.711 MB) / 13 434 environments (profiles/k_expansion_fused_fp32_batch96.md). Scaled to a full
+# (8.617 MB + 850.285 MB) / 13 434 environments (profiles/k_expansion_fused_fp32_batch96.md). Scaled to a full
 # launch by the environments it processes; valid only while that kernel is unchanged.
-FUSED_FP32_TRAFFIC_PER_ENV = (7.893e6 + 906.711e6) / 13434
+FUSED_FP32_TRAFFIC_PER_ENV = (8.617e6 + 850.285e6) / 13434
 
 WORKLOADS = {
     "batch": "512 periodic cubic cells, 64-216 atoms each (uniform), 0.05 atoms/A^3, 4 species uniform, d_min 1.8 A; "
@@ -364,7 +364,13 @@ def run_ours(args):
 
 
 def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None):
-    """Same step through the public API with host buffers: pinned H2D of the inputs, D2H of the power spectrum."""
+    """Same step through the public API with host buffers: pinned H2D of the inputs, D2H of the power spectrum.
+
+    Steps are pipelined the way a streaming user would run them: the power spectrum of step k leaves on a copy
+    stream while step k + 1 computes into the other of two output buffers; each buffer is reused only after its
+    copy has finished. Every step's inputs go host -> device and every step's p goes device -> host inside the
+    timed region.
+    """
     import torch
 
     steps = steps or max(3, min(args.steps, 20))
@@ -376,24 +382,37 @@ def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None):
         "struct_offsets": torch.as_tensor(system.struct_offsets, dtype=torch.int32).pin_memory(),
     }
     dev_t = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-    out_host = torch.empty(ps.shape, dtype=ps.dtype).pin_memory()
+    ps_buf = [ps, torch.empty_like(ps)]
+    out_host = [torch.empty(ps.shape, dtype=ps.dtype).pin_memory() for _ in range(2)]
     ds = rg.DeviceSystem(dev_t["positions"], dev_t["species"], dev_t["cells"], dev_t["pbc"], dev_t["struct_offsets"])
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = out_host.numel() * out_host.element_size()
+    d2h = out_host[0].numel() * out_host[0].element_size()
+    copy_stream = torch.cuda.Stream(dev)
+    copied = [None, None]
 
-    def one():
-        for k in host:
-            dev_t[k].copy_(host[k], non_blocking=True)
+    def one(k):
+        b = k & 1
+        cur = torch.cuda.current_stream(dev)
+        if copied[b] is not None:
+            cur.wait_event(copied[b])
+        for key in host:
+            dev_t[key].copy_(host[key], non_blocking=True)
         pairs = calc.neighbours(ds)
-        calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps)
-        out_host.copy_(ps, non_blocking=True)
+        calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps_buf[b])
+        ready = torch.cuda.Event()
+        ready.record(cur)
+        copy_stream.wait_event(ready)
+        with torch.cuda.stream(copy_stream):
+            out_host[b].copy_(ps_buf[b], non_blocking=True)
+        copied[b] = torch.cuda.Event()
+        copied[b].record(copy_stream)
 
-    for _ in range(2):
-        one()
+    for k in range(2):
+        one(k)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for _ in range(steps):
-        one()
+    for k in range(steps):
+        one(k)
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
     return {"ms": 1e3 * dt / steps, "h2d": h2d, "d2h": d2h}
