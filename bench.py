@@ -61,6 +61,14 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--structures", type=int, default=512, help="cells in the batch workload (profiling cases)")
+    ap.add_argument("--gradients", action="store_true",
+                    help="add the linear energy model and its forces and virial (rascal_linear_energy + rascal_gradients)")
+    ap.add_argument("--radial", choices=["spline", "exact", "mlp"], default="spline",
+                    help="radial integrals from the FP32 spline, the per-pair FP64 1F1, or the MLP surrogate "
+                         "(trained on the GPU before timing)")
+    ap.add_argument("--mlp-steps", type=int, default=4000, help="Adam steps of the surrogate's training (setup)")
+    ap.add_argument("--expansion-only", action="store_true",
+                    help="neighbours + coefficients only (rascal_spherical_expansion), no power spectrum")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -151,9 +159,17 @@ def cpu_worker(args):
     rng = np.random.default_rng(123)
     order = rng.permutation(system.n_atoms)
 
+    w = None
+    if args.gradients:
+        from synth import linear_weights
+
+        w = linear_weights(h.n_species, h.n_features("packed"), seed=4)
+
     def run(centres):
+        if w is not None:  # c, p, adjoint and per-pair gradients of the sampled centres' energy terms
+            return osoap.energy_gradients(system, h, w, centres=centres)
         c = osoap.spherical_expansion(system, h, centres=centres)
-        return osoap.power_spectrum(c, h, args.layout)
+        return c if args.expansion_only else osoap.power_spectrum(c, h, args.layout)
 
     run(order[:2])  # first call builds the oracle's per-(a, b) 1F1 switch points
     start, n = 2, 16
@@ -173,14 +189,17 @@ def cpu_baseline(args, cores=1):
     env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores),
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--config", args.config, "--layout", args.layout,
-           "--cpu-seconds", str(args.cpu_seconds)]
+           "--cpu-seconds", str(args.cpu_seconds)] + (["--gradients"] if args.gradients else []) + \
+          (["--expansion-only"] if args.expansion_only else [])
     res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     if res.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": res.stderr[-300:]}
     d = json.loads(res.stdout.strip().splitlines()[-1])
     return {"value": d["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{d['n']} seeded random centres of the {args.config} workload (neighbours + exact-1F1 coefficients "
-                      f"+ {args.layout} power spectrum, FP64 numpy), {d['seconds']:.1f} s on one host thread"}
+            "sample": f"{d['n']} seeded random centres of the {args.config} workload (neighbours + exact-1F1 coefficients"
+                      f"{'' if args.expansion_only else ' + ' + args.layout + ' power spectrum'}"
+                      f"{' + forces and virial' if args.gradients else ''}, FP64 numpy), "
+                      f"{d['seconds']:.1f} s on one host thread"}
 
 
 def run_reference(args):
@@ -195,10 +214,21 @@ def run_reference(args):
     h = osoap.Hypers(**system.hypers)
     rng = np.random.default_rng(7)
     order = rng.permutation(system.n_atoms)
-    osoap.power_spectrum(osoap.spherical_expansion(system, h, centres=order[:2]), h, args.layout)
+    w = None
+    if args.gradients:
+        from synth import linear_weights
+
+        w = linear_weights(h.n_species, h.n_features("packed"), seed=4)
+
+    def run(idx):
+        if w is not None:
+            return osoap.energy_gradients(system, h, w, centres=idx)
+        c = osoap.spherical_expansion(system, h, centres=idx)
+        return c if args.expansion_only else osoap.power_spectrum(c, h, args.layout)
+
+    run(order[:2])
     t0 = time.perf_counter()
-    c = osoap.spherical_expansion(system, h, centres=order[:4])
-    osoap.power_spectrum(c, h, args.layout)
+    run(order[:4])
     per = (time.perf_counter() - t0) / 4
     budget = 150.0
     per_step = max(1, int(budget / max(per, 1e-6) / (args.steps + args.warmup)))
@@ -208,8 +238,7 @@ def run_reference(args):
         nonlocal cursor
         idx = np.take(order, np.arange(cursor, cursor + per_step), mode="wrap")
         cursor += per_step
-        cc = osoap.spherical_expansion(system, h, centres=idx)
-        osoap.power_spectrum(cc, h, args.layout)
+        run(idx)
 
     for _ in range(args.warmup):
         step()
@@ -219,7 +248,9 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = per_step * args.steps / dt
     sample = (f"{per_step} seeded random centres per step of the {args.config} workload (neighbours + exact-1F1 "
-              f"coefficients + {args.layout} power spectrum, FP64 numpy), one host thread")
+              f"coefficients{'' if args.expansion_only else ' + ' + args.layout + ' power spectrum'}"
+              f"{' + forces and virial' if args.gradients else ''}, "
+              f"FP64 numpy), one host thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -250,27 +281,41 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     Qc = calc.coeffs_per_centre
     Fp = calc.n_features(args.layout)
+    if args.gradients and args.layout != "packed":
+        raise SystemExit("--gradients uses the linear model over the packed features (--layout packed)")
     coeffs = torch.empty((N, calc.n_species, calc.n_max, (calc.l_max + 1) ** 2), dtype=torch.float32, device=dev)
     ps = torch.empty((N, Fp), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    radial_info = radial_setup(args, calc, system, dev, rg)
+    weights = None
+    if args.gradients:
+        from synth import linear_weights
+
+        weights = torch.tensor(linear_weights(calc.n_species, calc.n_features("packed"), seed=4), dtype=torch.float32,
+                               device=dev)
 
     def step(events=None):
-        if events is not None:
-            events[0].record(stream)
-        pairs = calc.neighbours(ds)
-        if events is not None:
-            events[1].record(stream)
-        if args.separate:
-            calc.spherical_expansion(ds, pairs, out=coeffs)
+        # stage boundaries: neighbours | expansion (or fused soap) | power spectrum (separate form) | gradients
+        def mark(k):
             if events is not None:
-                events[2].record(stream)
-            calc.power_spectrum(coeffs, precision=args.ps, layout=args.layout, out=ps)
+                events[k].record(stream)
+
+        mark(0)
+        pairs = calc.neighbours(ds)
+        mark(1)
+        if args.separate or args.expansion_only:
+            calc.spherical_expansion(ds, pairs, out=coeffs)
+            mark(2)
+            if not args.expansion_only:
+                calc.power_spectrum(coeffs, precision=args.ps, layout=args.layout, out=ps)
         else:
             calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps)
-            if events is not None:
-                events[2].record(stream)
-        if events is not None:
-            events[3].record(stream)
+            mark(2)
+        mark(3)
+        if weights is not None:
+            calc.linear_energy(ds, ps, weights)
+            calc.gradients(ds, pairs, coeffs, weights=weights)
+        mark(4)
         return pairs
 
     for _ in range(max(args.warmup, 3)):
@@ -278,7 +323,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     n_pairs = pairs.n_pairs
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
@@ -295,8 +340,8 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = sampler.stop()
     launches = rg.launch_count() - launches0
-    stage = [[e[s].elapsed_time(e[s + 1]) for e in evs] for s in range(3)]
-    step_ms = [sum(stage[s][k] for s in range(3)) for k in range(args.steps)]
+    stage = [[e[s].elapsed_time(e[s + 1]) for e in evs] for s in range(4)]
+    step_ms = [sum(stage[s][k] for s in range(4)) for k in range(args.steps)]
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -305,32 +350,53 @@ def run_ours(args):
     total_env = N * world
     value = total_env / (ms * 1e-3)
 
-    # roofline of the dominant kernel: algorithmic bytes = inputs read + outputs written
+    # roofline of the dominant kernel: algorithmic bytes = inputs read + outputs written (HBM-bound kernels), or
+    # algorithmic FP32 flops (the gradient kernel)
     mean = [sum(x) / len(x) for x in stage]
     pair_in = 24 * n_pairs + 8 * (N + 1)                      # r_ji float4 + j + species(j); CSR offsets
     c_bytes = 4 * Qc * N
     p_bytes = 4 * Fp * N
-    fused = not args.separate
-    if fused:
-        kernel, alg, t_ms = "k_expansion<fused power spectrum> (rascal_soap)", pair_in + c_bytes + p_bytes, mean[1]
-        if mean[0] > mean[1]:
-            kernel, alg, t_ms = "rascal_neighbours", None, mean[0]
-    else:
-        cand = {"expansion": (pair_in + c_bytes, mean[1]), "power_spectrum": (c_bytes + p_bytes, mean[2])}
-        kernel = max(cand, key=lambda k: cand[k][1])
-        alg, t_ms = cand[kernel]
+    fused = not (args.separate or args.expansion_only)
     peak, peak_kind = load_peaks()
-    achieved = (alg / (t_ms * 1e-3) / 1e9) if alg else None
-    roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": (FUSED_FP32_TRAFFIC_PER_ENV * N if (fused and args.config == "batch" and args.ps == "fp32"
-                                                               and args.layout == "packed") else None),
-                "algorithmic_bytes_per_launch": alg, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
-                if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    peak_src = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s"
+    cand = {"rascal_neighbours": (None, mean[0])}
+    if fused:
+        cand["k_expansion<fused power spectrum> (rascal_soap)"] = (pair_in + c_bytes + p_bytes, mean[1])
+    else:
+        cand["k_expansion (rascal_spherical_expansion)"] = (pair_in + c_bytes, mean[1])
+        if not args.expansion_only:
+            cand["power spectrum (rascal_power_spectrum)"] = (c_bytes + p_bytes, mean[2])
+    if weights is not None:
+        cand["k_gradients (rascal_linear_energy + rascal_gradients)"] = (None, mean[3])
+    kernel = max(cand, key=lambda k: cand[k][1])
+    alg, t_ms = cand[kernel]
+    if kernel.startswith("k_gradients"):
+        # per pair: s += chat dR Y and w += chat R grad Y over the centre's species block, 2 + 3 FMA per (n, lm);
+        # per centre: the adjoint chat_l = k_l (W + W^T) C_l, Q x Q times Q x (2l+1)
+        n_lm = (calc.l_max + 1) ** 2
+        Q = calc.n_species * calc.n_max
+        flops = 10.0 * calc.n_max * n_lm * n_pairs + 2.0 * Q * Q * n_lm * N
+        sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+        alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock, TFLOP/s
+        achieved = flops / (t_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "traffic": None, "algorithmic_flops_per_launch": flops,
+                    "peak_source": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+    else:
+        achieved = (alg / (t_ms * 1e-3) / 1e9) if alg else None
+        traffic_known = (kernel.startswith("k_expansion<fused") and args.config == "batch" and args.ps == "fp32"
+                         and args.layout == "packed" and args.radial == "spline")
+        roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": (achieved / peak) if achieved else None,
+                    "traffic": FUSED_FP32_TRAFFIC_PER_ENV * N if traffic_known else None,
+                    "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
+    if radial_info.get("check_error"):
+        radial_info["c_err_vs_exact_fp64"] = coefficient_error(calc, ds, coeffs, rg, args)
+        del radial_info["check_error"]
 
     e2e = None
     if not args.no_e2e and world >= 1:
-        e2e = measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg)
+        e2e = measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, weights=weights)
         if world > 1:
             t = torch.tensor([e2e["ms"]], dtype=torch.float64, device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -345,11 +411,15 @@ def run_ours(args):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}", "global_batch": total_env,
-                       "env_per_gpu": N, "pairs_per_gpu": n_pairs, "layout": args.layout, "ps_precision": args.ps,
+                       "env_per_gpu": N, "pairs_per_gpu": n_pairs,
+                       "power_spectrum": None if args.expansion_only else {"layout": args.layout, "precision": args.ps,
+                                                                          "fused": fused},
+                       "gradients": bool(args.gradients), **radial_info,
                        "parallelism": f"dp{world} (independent batches per GPU)",
                        "l2": "256 MB buffer written before every timed step (L2 is 129 MB), outside the step events",
                        "stage_ms": {"neighbours": mean[0], ("expansion" if not fused else "soap"): mean[1],
-                                    **({"power_spectrum": mean[2]} if not fused else {})},
+                                    **({"power_spectrum": mean[2]} if args.separate else {}),
+                                    **({"gradients": mean[3]} if args.gradients else {})},
                        "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -363,7 +433,56 @@ def run_ours(args):
     return 0
 
 
-def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None):
+def radial_setup(args, calc, system, dev, rg):
+    """Selects the radial source. The MLP surrogate is trained on the GPU first (setup, outside the timed steps)."""
+    import torch
+
+    info = {"radial": args.radial}
+    if args.radial == "exact":
+        calc.set_radial("exact")
+    elif args.radial == "mlp":
+        from synth import mlp_initial_params, mlp_training_draws
+
+        F = calc.n_max * (calc.l_max + 1)
+        r_cut = float(system.hypers["r_cut"])
+        batch = 4096
+        r, order = mlp_training_draws(1 << 20, r_cut, batch, args.mlp_steps, seed=22)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        tgt, scale = calc.mlp_targets(torch.tensor(r))
+        calc.mlp_set_params(mlp_initial_params(calc.MLP_HIDDEN, F, seed=23), scale)
+        t = torch.tensor(r / r_cut, dtype=torch.float32, device=dev)
+        loss = calc.mlp_train(t, tgt, torch.tensor(order, device=dev), batch=batch, steps=args.mlp_steps, lr_max=1e-2,
+                              lr_min=1e-5, total_steps=args.mlp_steps)
+        torch.cuda.synchronize(dev)
+        info.update({"mlp_training": f"{args.mlp_steps} Adam steps (batch {batch}, cosine lr 1e-2 -> 1e-5) on 2^20 "
+                                     f"FP64-exact samples, r uniform in [0, {r_cut}] A",
+                     "mlp_setup_s": time.perf_counter() - t0, "mlp_final_loss": float(loss[-1].item())})
+        calc.set_radial("mlp")
+        info["check_error"] = True
+    return info
+
+
+def coefficient_error(calc, ds, coeffs, rg, args):
+    """Block max-relative errors of c (per centre and species block, max |dc| / max |c_ref|) of the timed radial
+    source and of the spline, both against the per-pair FP64 exact-1F1 path on the same GPU."""
+    def err(c, ref):
+        d = (c - ref).abs().flatten(2).amax(dim=2)
+        m = ref.abs().flatten(2).amax(dim=2)
+        ok = m > 0
+        return float((d[ok] / m[ok]).max().item())
+
+    pairs = calc.neighbours(ds)
+    calc.set_radial("exact")
+    ref = calc.spherical_expansion(ds, pairs)
+    calc.set_radial("spline")
+    spline = calc.spherical_expansion(ds, pairs)
+    calc.set_radial(args.radial)
+    mine = calc.spherical_expansion(ds, pairs)
+    return {args.radial: err(mine, ref), "spline": err(spline, ref)}
+
+
+def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None, weights=None):
     """Same step through the public API with host buffers: pinned H2D of the inputs, D2H of the power spectrum.
 
     Steps are pipelined the way a streaming user would run them: the power spectrum of step k leaves on a copy
@@ -382,11 +501,13 @@ def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None):
         "struct_offsets": torch.as_tensor(system.struct_offsets, dtype=torch.int32).pin_memory(),
     }
     dev_t = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-    ps_buf = [ps, torch.empty_like(ps)]
-    out_host = [torch.empty(ps.shape, dtype=ps.dtype).pin_memory() for _ in range(2)]
+    result = coeffs if args.expansion_only else ps  # the step's result read back by the host
+    ps_buf = [result, torch.empty_like(result)]
+    out_host = [torch.empty(result.shape, dtype=result.dtype).pin_memory() for _ in range(2)]
+    forces_host = torch.empty((system.n_atoms, 3), dtype=torch.float64).pin_memory()
     ds = rg.DeviceSystem(dev_t["positions"], dev_t["species"], dev_t["cells"], dev_t["pbc"], dev_t["struct_offsets"])
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = out_host[0].numel() * out_host[0].element_size()
+    d2h = out_host[0].numel() * out_host[0].element_size() + (forces_host.numel() * 8 if weights is not None else 0)
     copy_stream = torch.cuda.Stream(dev)
     copied = [None, None]
 
@@ -398,12 +519,24 @@ def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None):
         for key in host:
             dev_t[key].copy_(host[key], non_blocking=True)
         pairs = calc.neighbours(ds)
-        calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps_buf[b])
+        forces = None
+        if args.expansion_only:
+            calc.spherical_expansion(ds, pairs, out=ps_buf[b])
+        elif args.separate:
+            calc.spherical_expansion(ds, pairs, out=coeffs)
+            calc.power_spectrum(coeffs, precision=args.ps, layout=args.layout, out=ps_buf[b])
+        else:
+            calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps_buf[b])
+        if weights is not None:
+            calc.linear_energy(ds, ps_buf[b], weights)
+            forces, _ = calc.gradients(ds, pairs, coeffs, weights=weights)
         ready = torch.cuda.Event()
         ready.record(cur)
         copy_stream.wait_event(ready)
         with torch.cuda.stream(copy_stream):
             out_host[b].copy_(ps_buf[b], non_blocking=True)
+            if forces is not None:
+                forces_host.copy_(forces, non_blocking=True)
         copied[b] = torch.cuda.Event()
         copied[b].record(copy_stream)
 

@@ -183,7 +183,9 @@ int rascal_linear_energy(rascal_ctx* ctx, const rascal_system* sys, const float*
 /* Gradients of E = sum_i G_i . p_i (PACKED p) with respect to the positions and the cell (Appendix B).
  * Exactly one of d_grad_ps ([n_atoms][features_packed], G_i per centre) or d_weights ([n_species]
  * [features_packed], G_i = w_{a_i}, the linear model) must be non-NULL. The pair terms are recomputed per pair
- * from the spline and Y_lm; dc/dr is never stored.
+ * from the spline and Y_lm; dc/dr is never stored. Pair terms are summed in FP32 (per-atom force sums in a
+ * scratch FP32 array, per-centre virial sums in FP32) and written out as float64; structure sums are FP64.
+ * Calls with d_weights build dense symmetric per-species weight blocks in the context's scratch first.
  *   d_forces [n_atoms][3] float64: overwritten with F_k = -dE/dr_k (images of the centre add nothing)
  *   d_virial [n_structures][9] float64: overwritten with V[a][b] = sum_pairs dE/dr_ji[a] r_ji[b] */
 int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,

@@ -186,16 +186,18 @@ def adjoint_coefficients(c, hypers: Hypers, grad_p_packed):
     return chat.reshape(c.shape)
 
 
-def energy_gradients(system, hypers: Hypers, weights, radial_fn=None):
+def energy_gradients(system, hypers: Hypers, weights, radial_fn=None, centres=None):
     """Forces F = -dE/dr [N,3] and virial V = sum_pairs dE/dr_ji (x) r_ji [n_structures,3,3] for the linear model.
 
-    dE_i/dr_ji = sum_{n l m} chat^i_{a_j n l m} grad_r [f(r) I_nl(r) Y_lm(r^)], evaluated exactly per pair."""
+    dE_i/dr_ji = sum_{n l m} chat^i_{a_j n l m} grad_r [f(r) I_nl(r) Y_lm(r^)], evaluated exactly per pair.
+    centres: optional subset of centre atoms; the result is then the gradient of sum_{i in centres} E_i only."""
     h = hypers
-    nl = neighbour_list(system, h.r_cut)
+    nl = neighbour_list(system, h.r_cut, centres)
+    cidx = nl["centres"]
     c = spherical_expansion(system, h, nl=nl, radial_fn=radial_fn)
     a_all = h.species_index(system.species)
     p = power_spectrum(c, h, "packed")
-    grad_p = weights[a_all].reshape(p.shape)
+    grad_p = weights[a_all[cidx]].reshape(p.shape)
     chat = adjoint_coefficients(c, h, grad_p)                       # [N, S, n, lm]
     rij = nl["rij"]
     forces = np.zeros((system.n_atoms, 3))
@@ -208,9 +210,10 @@ def energy_gradients(system, hypers: Hypers, weights, radial_fn=None):
     I, dI = _radial(r, h, derivative=True, radial_fn=radial_fn)
     Y, dY = ylm.real_ylm(rij, h.l_max, gradient=True)
     lidx = np.array([l for l in range(h.l_max + 1) for _ in range(2 * l + 1)])
-    centre = np.repeat(np.arange(system.n_atoms), np.diff(nl["offsets"]))
+    centre_row = np.repeat(np.arange(cidx.size), np.diff(nl["offsets"]))
+    centre = cidx[centre_row]
     j = nl["nbr_j"]
-    ch = chat[centre, a_all[j]]                                     # [P, n, lm]
+    ch = chat[centre_row, a_all[j]]                                 # [P, n, lm]
     R = f[:, None, None] * I[:, :, lidx]                           # radial part f I, [P, n, lm]
     dR = (df[:, None, None] * I[:, :, lidx] + f[:, None, None] * dI[:, :, lidx])
     # grad [R Y] = dR/dr u Y + R grad Y

@@ -106,6 +106,7 @@ struct rascal_ctx {
 
     rascal::Arena scratch;  // grown on demand, reused across calls
     rascal::Arena scratch2;
+    rascal::Arena scratch_w;  // dense symmetric weight blocks of the gradient kernel
     int64_t* h_pinned;      // pinned host words for small read-backs
 
     rascal::ExpPlan plan;

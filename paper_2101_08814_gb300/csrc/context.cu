@@ -397,6 +397,7 @@ extern "C" void rascal_destroy(rascal_ctx* ctx) {
     cudaFreeHost(ctx->h_flags);
     cudaFreeHost(ctx->h_pinned);
     cudaFree(ctx->scratch.ptr);
+    cudaFree(ctx->scratch_w.ptr);
     cudaFree(ctx->scratch2.ptr);
     delete ctx;
 }

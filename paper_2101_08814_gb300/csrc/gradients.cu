@@ -13,43 +13,48 @@
 //   dE/dr_ji = s u + (w - (w.u) u)/|r|.
 // Forces: F_j -= dE/dr_ji, F_i += dE/dr_ji (skipped when j is an image of i: the two cancel, Appendix B);
 // virial V[a][b] += dE/dr_ji[a] r_ji[b] (images of i included).
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
 #include "ps_fp32.cuh"
+#include "tcgen05.cuh"
 #include "ylm_fp32.cuh"
 
 namespace rascal {
 
-// E_s = sum_{i in s} w_{a_i} . p_i, one CTA per centre, FP64 block reduction and one atomic per centre.
+// E_s = sum_{i in s} w_{a_i} . p_i, one CTA per centre, FP32 partial sums, FP64 across warps and one atomic per centre.
 __global__ void k_linear_energy(int N, int n_s, const int* __restrict__ offs, const int* __restrict__ species,
                                 const int* __restrict__ lut, const float* __restrict__ ps, const float* __restrict__ w,
                                 int64_t F, double* __restrict__ energy) {
     __shared__ double red[32];
     const int i = blockIdx.x;
+    int sid = 0;
+    if (threadIdx.x == 0) {  // structure of centre i, looked up first so that its latency overlaps the sum
+        int hi = n_s;
+        while (hi - sid > 1) {
+            const int mid = (sid + hi) >> 1;
+            if (offs[mid] <= i) sid = mid;
+            else hi = mid;
+        }
+    }
     const int lab = species[i];
     const int a = (lab >= 0 && lab < 256) ? lut[lab] : -1;
-    double acc = 0.0;
+    // FP32 partial sums per thread and warp (GB300's FP64 rate is a small fraction of its FP32 rate), FP64 across
+    // the warps and the structures
+    float acc = 0.0f;
     if (a >= 0) {
         const float* p = ps + (int64_t)i * F;
         const float* wa = w + (int64_t)a * F;
-        for (int64_t f = threadIdx.x; f < F; f += blockDim.x) acc += (double)p[f] * (double)wa[f];
+        for (int64_t f = threadIdx.x; f < F; f += blockDim.x) acc = fmaf(p[f], wa[f], acc);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)acc;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = n_s;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (offs[mid] <= i) lo = mid;
-                else hi = mid;
-            }
-            atomicAdd(&energy[lo], v);
-        }
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += red[k];
+        atomicAdd(&energy[sid], v);
     }
 }
 
@@ -67,7 +72,10 @@ struct GradArgs {
     const float* coeffs;
     const float* grad_ps;   // [N][Fp] or NULL
     const float* weights;   // [S][Fp] or NULL
-    double* forces;
+    const float* wsym;      // weights only: k_l (W_l + W_l^T) per species and l, dense [S][L1][Q][Qw] (Qw = ceil4(Q))
+    int Qw, Lp_adj, n_adj_tasks;
+    int adj_pref[kMaxLMax + 2];  // prefix counts of the adjoint tile tasks per l
+    float* forces;          // FP32 accumulation, converted to the FP64 output afterwards
     double* virial;
     unsigned* flags;
     int N, n_s, n_max, l_max, S, Q, n_lm, F, F_pad, n_pad, Lp, M, chunk, ps_norm;
@@ -92,63 +100,178 @@ __device__ inline void cutoff_and_slope(float r, float r_cut, float w, float& f,
 
 constexpr int kGradThreads = 256;
 
+// Dense symmetric adjoint weights: Ws[a][l][k][q] = k_l (W_l + W_l^T)[k][q] from the packed upper-triangular
+// weight rows (entry (q1 <= q2) at q1 (2Q - q1 - 1) / 2 + q2), zero in the padding columns q >= Q.
+__global__ void k_wsym(int S, int L1, int Q, int Qw, int ps_norm, const float* __restrict__ w, int64_t Fp,
+                       float* __restrict__ ws) {
+    const int64_t total = (int64_t)S * L1 * Q * Qw;
+    const int Qpk = Q * (Q + 1) / 2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e % Qw);
+        const int64_t r = e / Qw;
+        const int k = (int)(r % Q);
+        const int al = (int)(r / Q);
+        const int l = al % L1, a = al / L1;
+        float v = 0.0f;
+        if (q < Q) {
+            const int lo = min(q, k), hi = max(q, k);
+            v = w[(int64_t)a * Fp + (int64_t)l * Qpk + (lo * (2 * Q - lo - 1)) / 2 + hi];
+            if (q == k) v *= 2.0f;
+            if (ps_norm) v *= rsqrtf((float)(2 * l + 1));
+        }
+        ws[e] = v;
+    }
+}
+
+// One CTA per centre i:
+//   1. chat = k_l (W + W^T) C from the centre's coefficients (shared memory) and its weight block (global, L1);
+//   2. per chunk of the centre's pairs: stage r_ji, the neighbour's species, f_cut and f_cut';
+//      radial values (f I, (f I)') per pair (one warp per pair, lanes over (l, n));
+//      Y and dY/du per pair (warp w runs the m = w chains for all pairs, lanes over pairs);
+//      contraction s = sum_lm Y sum_n chat (f I)', w = sum_lm dY/du sum_n chat f I (one warp per pair, lanes over
+//      lm, warp-shuffle reduction);
+//      dE/dr_ji, the force scatter and the virial (one thread per pair).
 __global__ void __launch_bounds__(kGradThreads) k_gradients(const GradArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int chunk = A.chunk;
-    const size_t qn4 = ((size_t)A.Q * A.n_lm + 3) / 4 * 4;  // keeps the float4 arrays 16-byte aligned
-    float* s_C = reinterpret_cast<float*>(smem_raw);         // [Q][n_lm]
-    float* s_H = s_C + qn4;                                   // chat [Q][n_lm]
-    float4* s_vec = reinterpret_cast<float4*>(s_H + qn4);
-    float* s_G = reinterpret_cast<float*>(s_vec + chunk);    // [chunk][F_pad]   f I
-    float* s_D = s_G + (size_t)chunk * A.F_pad;               // [chunk][F_pad]   (f I)'
-    float* s_Y = s_D + (size_t)chunk * A.F_pad;               // [chunk][4][Lp]   Y, dY/dux, dY/duy, dY/duz
-    float* s_acc = s_Y + (size_t)chunk * 4 * A.Lp;            // [chunk][4]       s, wx, wy, wz
-    float* s_fc = s_acc + (size_t)chunk * 4;
+    const int QN = A.Q * A.n_lm;
+    const int QN4 = (QN + 3) & ~3;                            // keeps the float4 arrays 16-byte aligned
+    const int Yp = A.n_lm | 1;                                // odd pitch: conflict-free float4 rows
+    const int QL4 = A.wsym ? ((A.Q * A.Lp_adj + 3) & ~3) : QN4;
+    float* s_C = reinterpret_cast<float*>(smem_raw);          // [Q][n_lm], or [Q][Lp_adj] padded per l (tiled adjoint)
+    float* s_H = s_C + QL4;                                   // chat [Q][n_lm]
+    float4* s_vec = reinterpret_cast<float4*>(s_H + QN4);     // [chunk]
+    float4* s_Yv = s_vec + chunk;                             // [chunk][Yp]  (Y, dY/dux, dY/duy, dY/duz)
+    float4* s_acc = s_Yv + (size_t)chunk * Yp;                // [chunk]      (s, wx, wy, wz)
+    float2* s_GD = reinterpret_cast<float2*>(s_acc + chunk);  // [chunk][F_pad]  (f I, (f I)')
+    float* s_fc = reinterpret_cast<float*>(s_GD + (size_t)chunk * A.F_pad);
     float* s_dfc = s_fc + chunk;
     int* s_spc = reinterpret_cast<int*>(s_dfc + chunk);
     int* s_j = s_spc + chunk;
-    int* s_lp = s_j + chunk;
-    int* s_fmap = s_lp + (kMaxLMax + 2);
+    int* s_lofm = s_j + chunk;                                // [n_lm]  l of each lm
+    int* s_fmap = s_lofm + A.n_lm;                            // [F_pad]
     __shared__ double red[kGradThreads / 32][12];
+    __shared__ int s_sid;
 
     const int i = blockIdx.x;
+    if (threadIdx.x == 0) {  // structure of centre i, looked up early so that its latency overlaps the prologue
+        int lo = 0, hi = A.n_s;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (A.offs[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        s_sid = lo;
+    }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int L1 = A.l_max + 1;
-    if (tid < kMaxLMax + 2) s_lp[tid] = A.lp[tid];
+    for (int l = 0; l < L1; ++l)
+        for (int s = tid; s <= 2 * l; s += blockDim.x) s_lofm[l * l + s] = l;
     for (int t = tid; t < A.F_pad; t += blockDim.x) s_fmap[t] = A.fmap[t];
     const int lab_i = A.species[i];
     const int a_i = (lab_i >= 0 && lab_i < 256) ? A.lut[lab_i] : -1;
     const float* Gp = A.grad_ps ? A.grad_ps + (int64_t)i * A.Fp : (a_i >= 0 ? A.weights + (int64_t)a_i * A.Fp : nullptr);
-    const float* c = A.coeffs + (int64_t)i * A.Q * A.n_lm;
-    for (int e = tid; e < A.Q * A.n_lm; e += blockDim.x) s_C[e] = c[e];
+    const float* c = A.coeffs + (int64_t)i * QN;
+    const int Q = A.Q, n_lm = A.n_lm, Qpk = Q * (Q + 1) / 2;
+    if (A.wsym) {
+        // adjoint as 4 x 4 register tiles of chat_l = Ws_l C_l: C staged with every l block padded to a multiple of
+        // 4 columns (zeros), so that tiles load float4 rows of C and of the dense symmetric weights
+        const int Lq = A.Lp_adj;
+        for (int q = warp; q < Q; q += nwarps) {  // per row: lanes over the padded columns, l block by l block
+            for (int l = 0; l < L1; ++l) {
+                const int w = A.lp[l + 1] - A.lp[l];
+                for (int sx = lane; sx < w; sx += 32) {
+                    float* d = s_C + q * Lq + A.lp[l] + sx;
+                    if (sx <= 2 * l) cp_async4(d, c + q * n_lm + l * l + sx);
+                    else *d = 0.0f;
+                }
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        const int QT = (Q + 3) >> 2;
+        const float* Wsa = A.wsym + (int64_t)(a_i < 0 ? 0 : a_i) * L1 * Q * A.Qw;
+        for (int t = tid; t < A.n_adj_tasks && a_i >= 0; t += blockDim.x) {
+            int l = 0;
+            while (A.adj_pref[l + 1] <= t) ++l;
+            const int r = t - A.adj_pref[l];
+            const int st = r / QT, qt = r - st * QT;
+            const float* Wl = Wsa + (int64_t)l * Q * A.Qw + 4 * qt;
+            const float* Cl = s_C + A.lp[l] + 4 * st;
+            float acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+            for (int k = 0; k < Q; ++k) {
+                const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wl + k * A.Qw));
+                const float4 c4 = *reinterpret_cast<const float4*>(Cl + k * Lq);
+                const float ww[4] = {w4.x, w4.y, w4.z, w4.w}, cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ww[u], cc[v], acc[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = 4 * qt + u;
+                if (q >= Q) break;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int sx = 4 * st + v;
+                    if (sx <= 2 * l) s_H[q * n_lm + l * l + sx] = acc[u][v];
+                }
+            }
+        }
+        if (a_i < 0)
+            for (int e = tid; e < QN; e += blockDim.x) s_H[e] = 0.0f;
+    } else {
+    for (int e = tid; e < QN; e += blockDim.x) cp_async4(s_C + e, c + e);
+    cp_async_wait_all();
     __syncthreads();
-    // adjoint chat[q][lm] = k_l sum_q' (W + W^T)[q][q'] C[q'][lm]
-    const int Qpk = A.Q * (A.Q + 1) / 2;
-    for (int e = tid; e < A.Q * A.n_lm; e += blockDim.x) {
-        const int q = e / A.n_lm, lm = e - q * A.n_lm;
-        int l = 0;
-        while ((l + 1) * (l + 1) <= lm) ++l;
+    // adjoint chat[q][lm] = k_l sum_k (W + W^T)[q][k] C[k][lm]; the packed entry (q1 <= q2) sits at
+    // q1 (2Q - q1 - 1) / 2 + q2, and (W + W^T) doubles the diagonal
+    for (int e = tid; e < QN; e += blockDim.x) {
+        const int q = e / n_lm, lm = e - q * n_lm;
+        const int l = s_lofm[lm];
         float acc = 0.0f;
         if (Gp) {
             const float* W = Gp + (int64_t)l * Qpk;
-            for (int q2 = 0; q2 < A.Q; ++q2) {
-                const int lo = min(q, q2), hi = max(q, q2);
-                float wv = __ldg(&W[packed_index(lo, hi, A.Q)]);
-                if (q == q2) wv *= 2.0f;
-                acc = fmaf(wv, s_C[q2 * A.n_lm + lm], acc);
+            const float* Cc = s_C + lm;
+            int idx = q;  // entry (k, q), k < q
+            for (int k = 0; k < q; ++k) {
+                acc = fmaf(__ldg(W + idx), Cc[k * n_lm], acc);
+                idx += Q - k - 1;
             }
+            const int ro = (q * (2 * Q - q - 1)) / 2;  // entries (q, k), k >= q
+            acc = fmaf(2.0f * __ldg(W + ro + q), Cc[q * n_lm], acc);
+            for (int k = q + 1; k < Q; ++k) acc = fmaf(__ldg(W + ro + k), Cc[k * n_lm], acc);
         }
         s_H[e] = (A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f) * acc;
     }
-    double fi[3] = {0.0, 0.0, 0.0};
-    double vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    }
+    // FP32 per-thread and per-warp sums (GB300's FP64 rate is a small fraction of its FP32 rate); FP64 across warps
+    float fi[3] = {0.0f, 0.0f, 0.0f};
+    float vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int64_t seg_beg = A.offsets[i], seg_end = A.offsets[i + 1];
+    // the next chunk's r_ji and j are loaded into registers while the current chunk is processed
+    float4 nv = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+    int nj = 0;
+    if (tid < chunk && seg_beg + tid < seg_end) {
+        nv = A.rij[seg_beg + tid];
+        nj = A.nbr_j[seg_beg + tid];
+    }
     for (int64_t pos = seg_beg; pos < seg_end; pos += chunk) {
         const int nc = (int)((seg_end - pos) < (int64_t)chunk ? (seg_end - pos) : (int64_t)chunk);
         __syncthreads();
-        for (int t = tid; t < nc; t += blockDim.x) {
-            const float4 v = A.rij[pos + t];
-            const int j = A.nbr_j[pos + t];
+        if (tid < nc) {
+            const int t = tid;
+            const float4 v = nv;
+            const int j = nj;
+            if (pos + chunk + t < seg_end) {
+                nv = A.rij[pos + chunk + t];
+                nj = A.nbr_j[pos + chunk + t];
+            }
             const int lab = A.species[j];
             int a = (lab >= 0 && lab < 256) ? A.lut[lab] : -1;
             if (!(v.w > 1e-6f)) a = -1;
@@ -159,115 +282,109 @@ __global__ void __launch_bounds__(kGradThreads) k_gradients(const GradArgs A) {
             cutoff_and_slope(v.w, A.r_cut, A.width, f, df);
             s_fc[t] = f;
             s_dfc[t] = df;
-            s_acc[4 * t] = s_acc[4 * t + 1] = s_acc[4 * t + 2] = s_acc[4 * t + 3] = 0.0f;
         }
         __syncthreads();
-        // radial values and slopes: one warp per pair
-        for (int p = warp; p < nc; p += nwarps) {
-            const float r = s_vec[p].w, f = s_fc[p], df = s_dfc[p];
-            const float x = r * A.inv_delta;
-            int k = (int)x;
-            k = min(max(k, 0), A.M - 1);
-            const float u = x - (float)k;
-            const float4* trow = A.table + (int64_t)k * A.F;
-            for (int fp = lane; fp < A.F_pad; fp += 32) {
-                const int col = s_fmap[fp];
-                float g = 0.0f, dg = 0.0f;
-                if (col >= 0) {
-                    if (A.pre_G) {
-                        g = __ldg(&A.pre_G[(pos + p) * A.F + col]);
-                        dg = __ldg(&A.pre_D[(pos + p) * A.F + col]);
+        // radial values and slopes: one warp per pair, lanes over padded (l, n); the warps without a Y chain first
+        for (int p = nwarps - 1 - warp; p < nc; p += nwarps) {
+            const float f = s_fc[p], df = s_dfc[p];
+            float2* gd = s_GD + p * A.F_pad;
+            if (A.pre_G) {
+                const float* pg = A.pre_G + (pos + p) * A.F;
+                const float* pd = A.pre_D + (pos + p) * A.F;
+                for (int fp = lane; fp < A.F_pad; fp += 32) {
+                    const int col = s_fmap[fp];
+                    const float g = col >= 0 ? __ldg(pg + col) : 0.0f, dg = col >= 0 ? __ldg(pd + col) : 0.0f;
+                    gd[fp] = make_float2(f * g, df * g + f * dg);
+                }
+            } else {
+                const float x = s_vec[p].w * A.inv_delta;
+                const int k = min(max((int)x, 0), A.M - 1);
+                const float u = x - (float)k;
+                const float4* trow = A.table + k * A.F;
+                for (int fp = lane; fp < A.F_pad; fp += 32) {
+                    const int col = s_fmap[fp];
+                    const float4 cf = col >= 0 ? __ldg(trow + col) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    const float g = fmaf(u, fmaf(u, fmaf(u, cf.w, cf.z), cf.y), cf.x);
+                    const float dg = fmaf(u, fmaf(u, 3.0f * cf.w, 2.0f * cf.z), cf.y) * A.inv_delta;
+                    gd[fp] = make_float2(f * g, df * g + f * dg);
+                }
+            }
+        }
+        // Y and dY/du (gradient of the polynomial extension), forward mode through the recurrence: warp w runs the
+        // m = w chains, lanes over pairs
+        for (int m = warp; m < L1; m += nwarps) {
+            const float km = c_ylm_K[m], fm = (float)m;
+#pragma unroll 1
+            for (int p = lane; p < nc; p += 32) {
+                const float4 v = s_vec[p];
+                const float inv_r = v.w > 1e-6f ? 1.0f / v.w : 0.0f;
+                const float x = v.x * inv_r, y = v.y * inv_r, z = v.z * inv_r;
+                float cm = 1.0f, sm = 0.0f, cm1 = 0.0f, sm1 = 0.0f;  // (x+iy)^m and (x+iy)^(m-1)
+#pragma unroll 1
+                for (int t = 0; t < m; ++t) {
+                    cm1 = cm;
+                    sm1 = sm;
+                    const float nc2 = cm * x - sm * y;
+                    sm = cm * y + sm * x;
+                    cm = nc2;
+                }
+                float4* Yrow = s_Yv + p * Yp;
+                float q2 = 0.0f, q1 = km, d2 = 0.0f, d1 = 0.0f;
+#pragma unroll 1
+                for (int l = m; l < L1; ++l) {
+                    float q = q1, dq = d1;
+                    if (l > m) {
+                        const float Al = c_ylm_A[l * 16 + m], Bl = c_ylm_B[l * 16 + m];
+                        q = Al * (z * q1 - Bl * q2);
+                        dq = Al * (q1 + z * d1 - Bl * d2);
+                        q2 = q1;
+                        d2 = d1;
+                        q1 = q;
+                        d1 = dq;
+                    }
+                    const int l0 = l * l + l;
+                    if (m == 0) {
+                        Yrow[l0] = make_float4(q, 0.0f, 0.0f, dq);
                     } else {
-                        const float4 cf = __ldg(&trow[col]);
-                        g = fmaf(u, fmaf(u, fmaf(u, cf.w, cf.z), cf.y), cf.x);
-                        dg = fmaf(u, fmaf(u, 3.0f * cf.w, 2.0f * cf.z), cf.y) * A.inv_delta;
+                        Yrow[l0 + m] = make_float4(q * cm, q * fm * cm1, -q * fm * sm1, dq * cm);
+                        Yrow[l0 - m] = make_float4(q * sm, q * fm * sm1, q * fm * cm1, dq * sm);
                     }
                 }
-                s_G[(size_t)p * A.F_pad + fp] = f * g;
-                s_D[(size_t)p * A.F_pad + fp] = df * g + f * dg;
-            }
-        }
-        // Y and dY/du: one thread per (pair, m) chain, forward-mode through the recurrence
-        for (int idx = tid; idx < nc * L1; idx += blockDim.x) {
-            const int p = idx / L1, m = idx - p * L1;
-            const float4 v = s_vec[p];
-            const float inv_r = v.w > 1e-6f ? 1.0f / v.w : 0.0f;
-            const float x = v.x * inv_r, y = v.y * inv_r, z = v.z * inv_r;
-            float cm = 1.0f, sm = 0.0f, cm1 = 0.0f, sm1 = 0.0f;  // (x+iy)^m and (x+iy)^(m-1)
-            for (int t = 0; t < m; ++t) {
-                cm1 = cm;
-                sm1 = sm;
-                const float nc2 = cm * x - sm * y;
-                sm = cm * y + sm * x;
-                cm = nc2;
-            }
-            float* Y = s_Y + (size_t)p * 4 * A.Lp;
-            float* Yx = Y + A.Lp;
-            float* Yy = Yx + A.Lp;
-            float* Yz = Yy + A.Lp;
-            float q2 = 0.0f, q1 = c_ylm_K[m], d2 = 0.0f, d1 = 0.0f;
-            const float fm = (float)m;
-            for (int l = m; l <= A.l_max; ++l) {
-                float q, dq;
-                if (l == m) {
-                    q = q1;
-                    dq = 0.0f;
-                } else {
-                    const float Al = c_ylm_A[l * 16 + m], Bl = c_ylm_B[l * 16 + m];
-                    q = Al * (z * q1 - Bl * q2);
-                    dq = Al * (q1 + z * d1 - Bl * d2);
-                    q2 = q1;
-                    d2 = d1;
-                    q1 = q;
-                    d1 = dq;
-                }
-                if (m == 0) {
-                    const int s0 = s_lp[l] + l;
-                    Y[s0] = q;
-                    Yx[s0] = 0.0f;
-                    Yy[s0] = 0.0f;
-                    Yz[s0] = dq;
-                } else {
-                    const int sp = s_lp[l] + l + m, sn = s_lp[l] + l - m;
-                    Y[sp] = q * cm;
-                    Yx[sp] = q * fm * cm1;
-                    Yy[sp] = -q * fm * sm1;
-                    Yz[sp] = dq * cm;
-                    Y[sn] = q * sm;
-                    Yx[sn] = q * fm * sm1;
-                    Yy[sn] = q * fm * cm1;
-                    Yz[sn] = dq * sm;
-                }
             }
         }
         __syncthreads();
-        // contraction with chat: one thread per (pair, l)
-        for (int idx = tid; idx < nc * L1; idx += blockDim.x) {
-            const int p = idx / L1, l = idx - p * L1;
+        // contraction with chat: one warp per pair, lanes over lm
+        for (int p = warp; p < nc; p += nwarps) {
             const int a = s_spc[p];
-            if (a < 0) continue;
-            const float* H = s_H + (size_t)a * A.n_max * A.n_lm;
-            const float* G = s_G + (size_t)p * A.F_pad + l * A.n_pad;
-            const float* D = s_D + (size_t)p * A.F_pad + l * A.n_pad;
-            const float* Y = s_Y + (size_t)p * 4 * A.Lp + s_lp[l];
+            if (a < 0) continue;  // warp-uniform
+            const float* H = s_H + a * A.n_max * n_lm;
+            const float2* gd = s_GD + p * A.F_pad;
+            const float4* Yrow = s_Yv + p * Yp;
             float S = 0.0f, Wx = 0.0f, Wy = 0.0f, Wz = 0.0f;
-            for (int s = 0; s <= 2 * l; ++s) {
-                const int lm = l * l + s;
+            for (int lm = lane; lm < n_lm; lm += 32) {
+                const float2* g = gd + s_lofm[lm] * A.n_pad;
+                const float* h = H + lm;
                 float uu = 0.0f, vv = 0.0f;
                 for (int n = 0; n < A.n_max; ++n) {
-                    const float h = H[n * A.n_lm + lm];
-                    uu = fmaf(h, D[n], uu);
-                    vv = fmaf(h, G[n], vv);
+                    const float hv = h[n * n_lm];
+                    const float2 x = g[n];
+                    vv = fmaf(hv, x.x, vv);
+                    uu = fmaf(hv, x.y, uu);
                 }
-                S = fmaf(uu, Y[s], S);
-                Wx = fmaf(vv, Y[A.Lp + s], Wx);
-                Wy = fmaf(vv, Y[2 * A.Lp + s], Wy);
-                Wz = fmaf(vv, Y[3 * A.Lp + s], Wz);
+                const float4 y = Yrow[lm];
+                S = fmaf(uu, y.x, S);
+                Wx = fmaf(vv, y.y, Wx);
+                Wy = fmaf(vv, y.z, Wy);
+                Wz = fmaf(vv, y.w, Wz);
             }
-            atomicAdd(&s_acc[4 * p + 0], S);
-            atomicAdd(&s_acc[4 * p + 1], Wx);
-            atomicAdd(&s_acc[4 * p + 2], Wy);
-            atomicAdd(&s_acc[4 * p + 3], Wz);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                S += __shfl_xor_sync(0xffffffffu, S, o);
+                Wx += __shfl_xor_sync(0xffffffffu, Wx, o);
+                Wy += __shfl_xor_sync(0xffffffffu, Wy, o);
+                Wz += __shfl_xor_sync(0xffffffffu, Wz, o);
+            }
+            if (lane == 0) s_acc[p] = make_float4(S, Wx, Wy, Wz);
         }
         __syncthreads();
         // per pair: dE/dr_ji, force scatter, virial
@@ -276,51 +393,54 @@ __global__ void __launch_bounds__(kGradThreads) k_gradients(const GradArgs A) {
             const float4 v = s_vec[p];
             const float inv_r = 1.0f / v.w;
             const float ux = v.x * inv_r, uy = v.y * inv_r, uz = v.z * inv_r;
-            const float S = s_acc[4 * p], Wx = s_acc[4 * p + 1], Wy = s_acc[4 * p + 2], Wz = s_acc[4 * p + 3];
+            const float4 acc = s_acc[p];
+            const float S = acc.x, Wx = acc.y, Wy = acc.z, Wz = acc.w;
             const float wu = Wx * ux + Wy * uy + Wz * uz;
             const float g[3] = {S * ux + (Wx - wu * ux) * inv_r, S * uy + (Wy - wu * uy) * inv_r,
                                 S * uz + (Wz - wu * uz) * inv_r};
             const float rv[3] = {v.x, v.y, v.z};
             for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) vir[3 * a + b] += (double)g[a] * (double)rv[b];
+                for (int b = 0; b < 3; ++b) vir[3 * a + b] = fmaf(g[a], rv[b], vir[3 * a + b]);
             const int j = s_j[p];
             if (j != i) {
                 for (int a = 0; a < 3; ++a) {
-                    atomicAdd(&A.forces[3 * (int64_t)j + a], -(double)g[a]);
-                    fi[a] += (double)g[a];
+                    atomicAdd(&A.forces[3 * (int64_t)j + a], -g[a]);
+                    fi[a] += g[a];
                 }
             }
         }
     }
     // block reduction of F_i and the virial
-    double vals[12] = {fi[0], fi[1], fi[2], vir[0], vir[1], vir[2], vir[3], vir[4], vir[5], vir[6], vir[7], vir[8]};
+    float vals[12] = {fi[0], fi[1], fi[2], vir[0], vir[1], vir[2], vir[3], vir[4], vir[5], vir[6], vir[7], vir[8]};
 #pragma unroll
     for (int k = 0; k < 12; ++k)
         for (int o = 16; o > 0; o >>= 1) vals[k] += __shfl_xor_sync(0xffffffffu, vals[k], o);
     if (lane == 0)
-        for (int k = 0; k < 12; ++k) red[warp][k] = vals[k];
+        for (int k = 0; k < 12; ++k) red[warp][k] = (double)vals[k];
     __syncthreads();
     if (tid < 12) {
         double s = 0.0;
         for (int w = 0; w < nwarps; ++w) s += red[w][tid];
         if (tid < 3) {
-            if (s != 0.0) atomicAdd(&A.forces[3 * (int64_t)i + tid], s);
+            if (s != 0.0) atomicAdd(&A.forces[3 * (int64_t)i + tid], (float)s);
         } else {
-            int lo = 0, hi = A.n_s;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (A.offs[mid] <= i) lo = mid;
-                else hi = mid;
-            }
-            atomicAdd(&A.virial[9 * (int64_t)lo + (tid - 3)], s);
+            atomicAdd(&A.virial[9 * (int64_t)s_sid + (tid - 3)], s);
         }
     }
 }
 
-static size_t grad_smem(const rascal_ctx* ctx, int chunk) {
+__global__ void k_forces_f64(int64_t n, const float* __restrict__ f32, double* __restrict__ f64) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        f64[e] = (double)f32[e];
+}
+
+static size_t grad_smem(const rascal_ctx* ctx, int chunk, bool tiled) {
     const ExpPlan& P = ctx->plan;
-    return sizeof(float) * 2 * (((size_t)ctx->Q * ctx->n_lm + 3) / 4 * 4) + sizeof(float4) * chunk + sizeof(float) * chunk * (2 * P.F_pad + 4 * P.Lp + 4 + 2) +
-           sizeof(int) * (2 * chunk + kMaxLMax + 2 + P.F_pad) + 64;
+    const size_t QN4 = ((size_t)ctx->Q * ctx->n_lm + 3) / 4 * 4;
+    const size_t QL4 = tiled ? ((size_t)ctx->Q * P.Lp + 3) / 4 * 4 : QN4;
+    const size_t Yp = (size_t)(ctx->n_lm | 1);
+    return sizeof(float) * (QL4 + QN4) + sizeof(float4) * chunk * (1 + Yp + 1) + sizeof(float2) * chunk * P.F_pad +
+           sizeof(float) * 2 * chunk + sizeof(int) * (2 * chunk + ctx->n_lm + P.F_pad) + 64;
 }
 
 int gradients_setup(rascal_ctx* ctx) {
@@ -363,6 +483,17 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
     RASCAL_CUDA(cudaMemsetAsync(d_forces, 0, sizeof(double) * 3 * sys->n_atoms, ctx->stream));
     RASCAL_CUDA(cudaMemsetAsync(d_virial, 0, sizeof(double) * 9 * sys->n_structures, ctx->stream));
     if (sys->n_atoms == 0) return RASCAL_OK;
+    const int L1 = ctx->l_max + 1;
+    const int Qw = (ctx->Q + 3) / 4 * 4;
+    const size_t n_ws = d_weights ? (size_t)ctx->n_species * L1 * ctx->Q * Qw : 0;
+    void* wbase;
+    if ((st = arena_get(ctx->scratch_w, carve_bytes(sizeof(float) * 3 * (size_t)sys->n_atoms, sizeof(float) * n_ws),
+                        &wbase)))
+        return st;
+    Carver wcv(wbase);
+    float* f32 = wcv.take<float>(3 * (size_t)sys->n_atoms);
+    float* ws = wcv.take<float>(n_ws);
+    RASCAL_CUDA(cudaMemsetAsync(f32, 0, sizeof(float) * 3 * sys->n_atoms, ctx->stream));
     if (!d_offsets || !d_nbr_j || !d_rij || !d_coeffs) return set_error(RASCAL_E_ARG, "NULL device pointer");
     const ExpPlan& P = ctx->plan;
     GradArgs A;
@@ -377,7 +508,7 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
     A.coeffs = d_coeffs;
     A.grad_ps = d_grad_ps;
     A.weights = d_weights;
-    A.forces = d_forces;
+    A.forces = f32;
     A.virial = d_virial;
     A.flags = ctx->d_flags;
     A.N = sys->n_atoms;
@@ -398,13 +529,30 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
     A.r_cut = (float)ctx->r_cut;
     A.width = (float)ctx->smooth_width;
     for (int l = 0; l < kMaxLMax + 2; ++l) A.lp[l] = P.lp[l];
-    int chunk = 32;
-    while (chunk > 8 && grad_smem(ctx, chunk) > 200 * 1024) chunk /= 2;
+    A.wsym = nullptr;
+    if (d_weights) {  // dense symmetric adjoint weights per species and l, for the tiled adjoint
+        A.Qw = Qw;
+        A.Lp_adj = P.Lp;
+        const int blocks = (int)std::min<size_t>((n_ws + 255) / 256, 4096);
+        k_wsym<<<blocks, 256, 0, ctx->stream>>>(ctx->n_species, L1, ctx->Q, A.Qw, ctx->ps_norm, d_weights, A.Fp, ws);
+        RASCAL_LAUNCH_CHECK("k_wsym");
+        A.wsym = ws;
+        const int QT = (ctx->Q + 3) / 4;
+        A.adj_pref[0] = 0;
+        for (int l = 0; l < L1; ++l) A.adj_pref[l + 1] = A.adj_pref[l] + QT * ((2 * l + 1 + 3) / 4);
+        for (int l = L1; l < kMaxLMax + 1; ++l) A.adj_pref[l + 1] = A.adj_pref[l];
+        A.n_adj_tasks = A.adj_pref[L1];
+    }
+    int chunk = 32;  // four CTAs per SM where the hypers allow it
+    while (chunk > 8 && grad_smem(ctx, chunk, A.wsym != nullptr) > 56 * 1024) chunk /= 2;
     A.chunk = chunk;
-    const size_t smem = grad_smem(ctx, chunk);
+    const size_t smem = grad_smem(ctx, chunk, A.wsym != nullptr);
     if (smem > 220 * 1024) return set_error(RASCAL_E_UNSUPPORTED, "hypers too large for the gradient kernel");
     if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, true, &A.pre_G, &A.pre_D))) return st;
     k_gradients<<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A);
     RASCAL_LAUNCH_CHECK("k_gradients");
+    const int64_t n3 = 3 * (int64_t)sys->n_atoms;
+    k_forces_f64<<<(unsigned)std::min<int64_t>((n3 + 255) / 256, 8192), 256, 0, ctx->stream>>>(n3, f32, d_forces);
+    RASCAL_LAUNCH_CHECK("k_forces_f64");
     return RASCAL_OK;
 }

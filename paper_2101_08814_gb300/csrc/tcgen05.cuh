@@ -116,4 +116,11 @@ __device__ inline void bulk_wait_read() {
 }
 __device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// 4-byte asynchronous global -> shared copy (no register round trip, many in flight per thread); cp_async_wait_all
+// then a barrier make the copies visible to the CTA.
+__device__ inline void cp_async4(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 }  // namespace rascal

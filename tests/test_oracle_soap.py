@@ -159,6 +159,20 @@ def test_forces_and_virial_against_finite_differences():
     assert np.allclose(V[0], fdV, atol=1e-5 * max(1.0, np.max(np.abs(fdV))))
 
 
+def test_gradients_of_a_centre_subset_add_up_to_the_whole():
+    # E is a sum over centres, so the gradients of the energy terms of a partition of the centres add up to the
+    # gradients of E; the partial sums are what the timed CPU samples compute
+    s = small_cell_system(seed=5, n_atoms=7, L=5.6, hypers=dict(r_cut=4.5, sigma=0.45, n_max=3, l_max=3, smooth_width=0.5, species=[1, 6]))
+    h = soap.Hypers(**s.hypers)
+    w = linear_weights(h.n_species, h.n_features("packed"), seed=6)
+    F, V = soap.energy_gradients(s, h, w)
+    Fa, Va = soap.energy_gradients(s, h, w, centres=[0, 2, 5])
+    Fb, Vb = soap.energy_gradients(s, h, w, centres=[6, 1, 3, 4])
+    assert np.allclose(Fa + Fb, F, atol=1e-12 * np.max(np.abs(F)))
+    assert np.allclose(Va + Vb, V, atol=1e-12 * np.max(np.abs(V)))
+    assert not np.allclose(Fa, F)
+
+
 def test_self_images_give_no_force_but_virial():
     # one atom in a cell narrower than r_cut: the environment holds only images of the atom itself
     cell = np.array([[3.1, 0.0, 0.0], [0.4, 3.3, 0.0], [0.2, -0.5, 3.6]])
