@@ -147,6 +147,31 @@ def dist_init(args):
     return rank, world, local
 
 
+def _over_ranks(x, device, op):
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()) or \
+            torch.distributed.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=op)
+    return float(t.item())
+
+
+def max_over_ranks(x, device):
+    """Largest value over the ranks: the slowest rank sets the job's time. The only collective of a run."""
+    import torch
+
+    return _over_ranks(x, device, torch.distributed.ReduceOp.MAX)
+
+
+def sum_over_ranks(x, device):
+    """Sum over the ranks (environments processed by the whole job: each rank has its own batch)."""
+    import torch
+
+    return _over_ranks(x, device, torch.distributed.ReduceOp.SUM)
+
+
 # ---------------------------------------------------------------------------------------------------- CPU oracle
 def cpu_worker(args):
     """Times the FP64 oracle on a bounded, seeded sample of centres of the workload (single host thread)."""
@@ -343,11 +368,8 @@ def run_ours(args):
     stage = [[e[s].elapsed_time(e[s + 1]) for e in evs] for s in range(4)]
     step_ms = [sum(stage[s][k] for s in range(4)) for k in range(args.steps)]
     ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    total_env = N * world
+    ms = max_over_ranks(ms, dev)
+    total_env = int(sum_over_ranks(N, dev))
     value = total_env / (ms * 1e-3)
 
     # roofline of the dominant kernel: algorithmic bytes = inputs read + outputs written (HBM-bound kernels), or
@@ -397,10 +419,7 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e and world >= 1:
         e2e = measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, weights=weights)
-        if world > 1:
-            t = torch.tensor([e2e["ms"]], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e["ms"] = float(t.item())
+        e2e["ms"] = max_over_ranks(e2e["ms"], dev)
         e2e = {"value": total_env / (e2e["ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e["ms"]}
 
