@@ -148,7 +148,11 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         }
         tc_fence_before();
     }
-    const int64_t seg_beg = A.offsets[i], seg_end = A.offsets[i + 1];
+    const int64_t seg_beg = A.offsets[i];
+    const int seg_len = (int)(A.offsets[i + 1] - seg_beg);
+    const float4* seg_rij = A.rij + seg_beg;
+    const int* seg_j = A.nbr_j + seg_beg;
+    const float* seg_G = A.pre_G ? A.pre_G + seg_beg * A.F : nullptr;
     const int L1 = A.l_max + 1;
 
     int my_l = 0, my_nt = 0, my_mt = 0;
@@ -169,18 +173,16 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         const int a0 = round * A.S_c;
         const int na = min(A.S_c, A.S - a0);
         const bool active = (g < na) && (task < A.T_s);
-        float acc[4][4];
+        uint64_t ap[4][2];  // the thread's 4 x 4 tile as (v, v+1) pairs of FP32 sums
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+        for (int u = 0; u < 4; ++u) ap[u][0] = ap[u][1] = 0ull;
 
-        for (int64_t pos = seg_beg; pos < seg_end; pos += chunk) {
-            const int nc = (int)((seg_end - pos) < (int64_t)chunk ? (seg_end - pos) : (int64_t)chunk);
+        for (int pos = 0; pos < seg_len; pos += chunk) {  // pair offsets relative to the centre's segment
+            const int nc = min(chunk, seg_len - pos);
             #pragma unroll 1
             for (int t = tid; t < nc; t += blockDim.x) {
-                const float4 v = A.rij[pos + t];
-                const int j = A.nbr_j[pos + t];
+                const float4 v = seg_rij[pos + t];
+                const int j = seg_j[pos + t];
                 const int lab = A.species[j];
                 int a = (lab >= 0 && lab < 256) ? A.lut[lab] : -1;
                 if (a < 0) atomicOr(A.flags, kFlagSpecies);
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 const float fc = s_fc[p];
                 float* grow = s_G + q * A.F_pad;
                 if (A.pre_G) {  // per-pair values (EXACT / MLP radial modes)
-                    const float* prow = A.pre_G + (pos + p) * A.F;
+                    const float* prow = seg_G + (pos + p) * A.F;
                     for (int fp = lane; fp < A.F_pad; fp += 32) {
                         const int col = s_fmap[fp];
                         grow[fp] = col >= 0 ? fc * __ldg(prow + col) : 0.0f;
@@ -279,12 +281,6 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
             __syncthreads();
             if (active) {
                 const int beg = s_start[g], end = s_start[g + 1];
-                uint64_t ap[4][2];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    ap[u][0] = f2_pack(acc[u][0], acc[u][1]);
-                    ap[u][1] = f2_pack(acc[u][2], acc[u][3]);
-                }
                 for (int q = beg; q < end; ++q) {
                     const float4 gv = *reinterpret_cast<const float4*>(s_G + q * A.F_pad + g_off);
                     const float4 yv = *reinterpret_cast<const float4*>(s_Y + q * A.Ly + y_off);
@@ -297,13 +293,14 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                         ap[u][1] = f2_fma(gu, y23, ap[u][1]);
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    f2_unpack(ap[u][0], acc[u][0], acc[u][1]);
-                    f2_unpack(ap[u][1], acc[u][2], acc[u][3]);
-                }
             }
             __syncthreads();
+        }
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            f2_unpack(ap[u][0], acc[u][0], acc[u][1]);
+            f2_unpack(ap[u][1], acc[u][2], acc[u][3]);
         }
         if (active) {
             const int a = a0 + g;
