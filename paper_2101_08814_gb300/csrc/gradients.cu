@@ -165,8 +165,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradients(const GradArgs A) {
     }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int L1 = A.l_max + 1;
-    for (int l = 0; l < L1; ++l)
-        for (int s = tid; s <= 2 * l; s += blockDim.x) s_lofm[l * l + s] = l;
+    for (int lm = tid; lm < A.n_lm; lm += blockDim.x) s_lofm[lm] = (int)sqrtf((float)lm);  // l with l^2 <= lm
     for (int t = tid; t < A.F_pad; t += blockDim.x) s_fmap[t] = A.fmap[t];
     const int lab_i = A.species[i];
     const int a_i = (lab_i >= 0 && lab_i < 256) ? A.lut[lab_i] : -1;
@@ -177,16 +176,13 @@ __global__ void __launch_bounds__(kGradThreads) k_gradients(const GradArgs A) {
         // adjoint as 4 x 4 register tiles of chat_l = Ws_l C_l: C staged with every l block padded to a multiple of
         // 4 columns (zeros), so that tiles load float4 rows of C and of the dense symmetric weights
         const int Lq = A.Lp_adj;
-        for (int q = warp; q < Q; q += nwarps) {  // per row: lanes over the padded columns, l block by l block
-            for (int l = 0; l < L1; ++l) {
-                const int w = A.lp[l + 1] - A.lp[l];
-                for (int sx = lane; sx < w; sx += 32) {
-                    float* d = s_C + q * Lq + A.lp[l] + sx;
-                    if (sx <= 2 * l) cp_async4(d, c + q * n_lm + l * l + sx);
-                    else *d = 0.0f;
-                }
+        for (int e = tid; e < Q * Lq; e += blockDim.x) s_C[e] = 0.0f;  // padding columns read as zero
+        __syncthreads();
+        for (int q = warp; q < Q; q += nwarps)  // per row: lanes over lm
+            for (int lm = lane; lm < n_lm; lm += 32) {
+                const int l = s_lofm[lm];
+                cp_async4(s_C + q * Lq + A.lp[l] + (lm - l * l), c + q * n_lm + lm);
             }
-        }
         cp_async_wait_all();
         __syncthreads();
         const int QT = (Q + 3) >> 2;
@@ -411,16 +407,18 @@ __global__ void __launch_bounds__(kGradThreads) k_gradients(const GradArgs A) {
         }
     }
     // block reduction of F_i and the virial
-    float vals[12] = {fi[0], fi[1], fi[2], vir[0], vir[1], vir[2], vir[3], vir[4], vir[5], vir[6], vir[7], vir[8]};
+    // the per-pair phase runs on threads < chunk <= 32, so warp 0 holds all the partial sums
+    if (warp == 0) {
+        float vals[12] = {fi[0], fi[1], fi[2], vir[0], vir[1], vir[2], vir[3], vir[4], vir[5], vir[6], vir[7], vir[8]};
 #pragma unroll
-    for (int k = 0; k < 12; ++k)
-        for (int o = 16; o > 0; o >>= 1) vals[k] += __shfl_xor_sync(0xffffffffu, vals[k], o);
-    if (lane == 0)
-        for (int k = 0; k < 12; ++k) red[warp][k] = (double)vals[k];
+        for (int k = 0; k < 12; ++k)
+            for (int o = 16; o > 0; o >>= 1) vals[k] += __shfl_xor_sync(0xffffffffu, vals[k], o);
+        if (lane == 0)
+            for (int k = 0; k < 12; ++k) red[0][k] = (double)vals[k];
+    }
     __syncthreads();
     if (tid < 12) {
-        double s = 0.0;
-        for (int w = 0; w < nwarps; ++w) s += red[w][tid];
+        const double s = red[0][tid];
         if (tid < 3) {
             if (s != 0.0) atomicAdd(&A.forces[3 * (int64_t)i + tid], (float)s);
         } else {
@@ -543,7 +541,7 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
         for (int l = L1; l < kMaxLMax + 1; ++l) A.adj_pref[l + 1] = A.adj_pref[l];
         A.n_adj_tasks = A.adj_pref[L1];
     }
-    int chunk = 32;  // four CTAs per SM where the hypers allow it
+    int chunk = 32;  // four CTAs per SM where the hypers allow it; never above 32 (warp 0 runs the per-pair phase)
     while (chunk > 8 && grad_smem(ctx, chunk, A.wsym != nullptr) > 56 * 1024) chunk /= 2;
     A.chunk = chunk;
     const size_t smem = grad_smem(ctx, chunk, A.wsym != nullptr);
