@@ -74,6 +74,7 @@ struct GradArgs {
     const float* weights;   // [S][Fp] or NULL
     const float* wsym;      // weights only: k_l (W_l + W_l^T) per species and l, dense [S][L1][Q][Qw] (Qw = ceil4(Q))
     int Qw, Lp_adj, n_adj_tasks;
+    int aux_off;            // bytes from the pair area to the small tables (past both the pair area and C)
     int adj_pref[kMaxLMax + 2];  // prefix counts of the adjoint tile tasks per l
     float* forces;          // FP32 accumulation, converted to the FP64 output afterwards
     double* virial;
@@ -137,9 +138,9 @@ __global__ void __launch_bounds__(kGradThreads) k_gradients(const GradArgs A) {
     const int QN = A.Q * A.n_lm;
     const int QN4 = (QN + 3) & ~3;                            // keeps the float4 arrays 16-byte aligned
     const int Yp = A.n_lm | 1;                                // odd pitch: conflict-free float4 rows
-    const int QL4 = A.wsym ? ((A.Q * A.Lp_adj + 3) & ~3) : QN4;
-    float* s_C = reinterpret_cast<float*>(smem_raw);          // [Q][n_lm], or [Q][Lp_adj] padded per l (tiled adjoint)
-    float* s_H = s_C + QL4;                                   // chat [Q][n_lm]
+    float* s_H = reinterpret_cast<float*>(smem_raw);          // chat [Q][n_lm]
+    // the coefficients are needed only by the adjoint, before the pair loop: they share the pair area
+    float* s_C = s_H + QN4;                                   // [Q][n_lm], or [Q][Lp_adj] padded per l (tiled adjoint)
     float4* s_vec = reinterpret_cast<float4*>(s_H + QN4);     // [chunk]
     float4* s_Yv = s_vec + chunk;                             // [chunk][Yp]  (Y, dY/dux, dY/duy, dY/duz)
     float4* s_acc = s_Yv + (size_t)chunk * Yp;                // [chunk]      (s, wx, wy, wz)
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradients(const GradArgs A) {
     float* s_dfc = s_fc + chunk;
     int* s_spc = reinterpret_cast<int*>(s_dfc + chunk);
     int* s_j = s_spc + chunk;
-    int* s_lofm = s_j + chunk;                                // [n_lm]  l of each lm
+    int* s_lofm = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(s_vec) + A.aux_off);  // [n_lm] l of lm
     int* s_fmap = s_lofm + A.n_lm;                            // [F_pad]
     __shared__ double red[kGradThreads / 32][12];
     __shared__ int s_sid;
@@ -432,13 +433,21 @@ __global__ void k_forces_f64(int64_t n, const float* __restrict__ f32, double* _
         f64[e] = (double)f32[e];
 }
 
-static size_t grad_smem(const rascal_ctx* ctx, int chunk, bool tiled) {
+// bytes from the pair area to the small tables: the larger of the pair area and the staged coefficients
+static size_t grad_aux_off(const rascal_ctx* ctx, int chunk, bool tiled) {
     const ExpPlan& P = ctx->plan;
     const size_t QN4 = ((size_t)ctx->Q * ctx->n_lm + 3) / 4 * 4;
     const size_t QL4 = tiled ? ((size_t)ctx->Q * P.Lp + 3) / 4 * 4 : QN4;
     const size_t Yp = (size_t)(ctx->n_lm | 1);
-    return sizeof(float) * (QL4 + QN4) + sizeof(float4) * chunk * (1 + Yp + 1) + sizeof(float2) * chunk * P.F_pad +
-           sizeof(float) * 2 * chunk + sizeof(int) * (2 * chunk + ctx->n_lm + P.F_pad) + 64;
+    const size_t pair_area = sizeof(float4) * chunk * (1 + Yp + 1) + sizeof(float2) * chunk * P.F_pad +
+                             sizeof(float) * 2 * chunk + sizeof(int) * 2 * chunk;
+    return align_up(std::max(pair_area, sizeof(float) * QL4), 16);
+}
+
+static size_t grad_smem(const rascal_ctx* ctx, int chunk, bool tiled) {
+    const ExpPlan& P = ctx->plan;
+    const size_t QN4 = ((size_t)ctx->Q * ctx->n_lm + 3) / 4 * 4;
+    return sizeof(float) * QN4 + grad_aux_off(ctx, chunk, tiled) + sizeof(int) * (ctx->n_lm + P.F_pad) + 64;
 }
 
 int gradients_setup(rascal_ctx* ctx) {
@@ -541,9 +550,11 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
         for (int l = L1; l < kMaxLMax + 1; ++l) A.adj_pref[l + 1] = A.adj_pref[l];
         A.n_adj_tasks = A.adj_pref[L1];
     }
-    int chunk = 32;  // four CTAs per SM where the hypers allow it; never above 32 (warp 0 runs the per-pair phase)
-    while (chunk > 8 && grad_smem(ctx, chunk, A.wsym != nullptr) > 56 * 1024) chunk /= 2;
+    // the largest chunk (<= 32: warp 0 runs the per-pair phase) that keeps four CTAs per SM
+    int chunk = 32;
+    while (chunk > 1 && grad_smem(ctx, chunk, A.wsym != nullptr) > 56 * 1024) --chunk;
     A.chunk = chunk;
+    A.aux_off = (int)grad_aux_off(ctx, chunk, A.wsym != nullptr);
     const size_t smem = grad_smem(ctx, chunk, A.wsym != nullptr);
     if (smem > 220 * 1024) return set_error(RASCAL_E_UNSUPPORTED, "hypers too large for the gradient kernel");
     if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, true, &A.pre_G, &A.pre_D))) return st;
