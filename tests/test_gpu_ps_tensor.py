@@ -87,3 +87,26 @@ def test_batch_full_size_sampled(rg):
     s = config_batch()
     rng = np.random.default_rng(2)
     _check(rg, s, layouts=("packed",), centres=np.concatenate([[0, s.n_atoms - 1], rng.choice(s.n_atoms, 30, replace=False)]))
+
+
+def test_isolated_atoms_and_crowded_centres(rg):
+    # a dense cluster (centres with more neighbours than one staged chunk) next to atoms with no neighbour at all:
+    # the isolated centres' c and p are exactly zero in every form, the crowded ones match the oracle
+    rng = np.random.Generator(np.random.PCG64(17))
+    L = 40.0
+    cluster = random_cell_atoms(70, np.eye(3) * 9.0, 1.05, rng) + 4.0
+    lone = np.array([[30.0, 30.0, 30.0], [30.0, 8.0, 30.0], [8.0, 30.0, 20.0]])
+    pos = np.concatenate([cluster, lone])
+    spe = np.where(rng.random(len(pos)) < 0.5, 1, 8).astype(np.int32)
+    s = System(pos, spe, (np.eye(3) * L)[None], np.zeros((1, 3), np.int32), np.array([0, len(pos)], np.int32),
+               dict(r_cut=5.0, sigma=0.5, n_max=6, l_max=5, smooth_width=0.5, species=[1, 8]))
+    calc = rg.SoapCalculator(**s.hypers)
+    ds = rg.DeviceSystem.from_numpy(s)
+    pairs = calc.neighbours(ds)
+    counts = np.diff(pairs.offsets.cpu().numpy())
+    assert counts.max() > 32 and np.all(counts[-3:] == 0)
+    _check(rg, s)
+    for prec in ("fp32", "bf16", "tf32x3"):
+        c, p = calc.soap(ds, pairs, precision=prec)
+        calc.sync()
+        assert np.all(c.cpu().numpy()[-3:] == 0.0) and np.all(p.cpu().numpy()[-3:] == 0.0), prec
