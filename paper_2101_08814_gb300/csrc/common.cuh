@@ -178,6 +178,8 @@ int radial_precompute(rascal_ctx* ctx, const rascal_system* sys, const int64_t* 
 int mlp_setup(rascal_ctx* ctx);
 int expansion_setup(rascal_ctx* ctx);
 int power_spectrum_setup(rascal_ctx* ctx);
+// BF16 / TF32x3 power spectrum of given coefficients [n][Q][n_lm] by the fused kernel's tensor-core Gram
+int power_spectrum_tc(rascal_ctx* ctx, int64_t n_centres, const float* d_coeffs, int precision, int layout, float* d_ps);
 int gradients_setup(rascal_ctx* ctx);
 
 }  // namespace rascal

@@ -42,6 +42,7 @@ struct ExpArgs {
     const int* lut;
     const float4* table;
     const float* pre_G;  // per-pair radial values [P][F] (EXACT / MLP modes) or NULL (spline table)
+    const float* c_in;   // tensor-core power spectrum of given coefficients [N][Q][n_lm]: no pair phase, or NULL
     const int* tasks;
     const int* fmap;
     float* coeffs;
@@ -91,14 +92,17 @@ __device__ inline void store_staged(float* dst, const float* st, int count) {
     if (t >= 4 && t < 4 + tail) dst[head + body + t - 4] = st[head + body + t - 4];
 }
 
-// CTA-wide copy of count floats from shared memory (16-byte aligned) to global memory, by float4 when dst allows
-__device__ inline void copy_out(float* __restrict__ dst, const float* __restrict__ src, int count) {
-    if (((reinterpret_cast<uintptr_t>(dst) & 15) | (count & 3)) == 0) {
-        const float4* s4 = reinterpret_cast<const float4*>(src);
-        float4* d4 = reinterpret_cast<float4*>(dst);
-        for (int t = threadIdx.x; t < (count >> 2); t += blockDim.x) d4[t] = s4[t];
+// element (q, s) of C_l into the K-major operand tile of l (BF16, or TF32 hi/lo for the three-MMA split)
+template <int GRAM>
+__device__ inline void put_operand(unsigned char* tiles, const ExpArgs& A, int l, int q, int s, float cv) {
+    constexpr int esz = (GRAM == kGramTf32x3) ? 4 : 2, e16 = 16 / esz;
+    const int off = A.tile_off[l] + (q >> 3) * A.sbo[l] + (s / e16) * 128 + (q & 7) * 16 + (s % e16) * esz;
+    if (GRAM == kGramTf32x3) {
+        const float hi = __uint_as_float(__float_as_uint(cv) & 0xFFFFE000u);
+        *reinterpret_cast<float*>(tiles + off) = hi;
+        *reinterpret_cast<float*>(tiles + A.lo_off + off) = cv - hi;
     } else {
-        for (int t = threadIdx.x; t < count; t += blockDim.x) dst[t] = src[t];
+        *reinterpret_cast<__nv_bfloat16*>(tiles + off) = __float2bfloat16_rn(cv);
     }
 }
 
@@ -148,8 +152,9 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         }
         tc_fence_before();
     }
-    const int64_t seg_beg = A.offsets[i];
-    const int seg_len = (int)(A.offsets[i + 1] - seg_beg);
+    const bool given_c = TC && A.c_in != nullptr;  // power spectrum of given coefficients: no pairs
+    const int64_t seg_beg = given_c ? 0 : A.offsets[i];
+    const int seg_len = given_c ? 0 : (int)(A.offsets[i + 1] - seg_beg);
     const float4* seg_rij = A.rij + seg_beg;
     const int* seg_j = A.nbr_j + seg_beg;
     const float* seg_G = A.pre_G ? A.pre_G + seg_beg * A.F : nullptr;
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
     const int g_off = my_l * A.n_pad + 4 * my_nt;   // offset inside a G row
     const int y_off = s_lp[my_l] + 4 * my_mt;       // offset inside a Y row
 
-    for (int round = 0; round < A.rounds; ++round) {
+    for (int round = 0; round < (given_c ? 0 : A.rounds); ++round) {
         const int a0 = round * A.S_c;
         const int na = min(A.S_c, A.S - a0);
         const bool active = (g < na) && (task < A.T_s);
@@ -346,22 +351,20 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     if (s > 2 * my_l) continue;
                     const float cv = acc[u][v];
                     out[n * A.n_lm + s] = cv;
-                    if (TC) {
-                        constexpr int esz = (GRAM == kGramTf32x3) ? 4 : 2, e16 = 16 / esz;
-                        const int off = A.tile_off[my_l] + (q >> 3) * A.sbo[my_l] + (s / e16) * 128 + (q & 7) * 16 + (s % e16) * esz;
-                        if (GRAM == kGramTf32x3) {
-                            const float hi = __uint_as_float(__float_as_uint(cv) & 0xFFFFE000u);
-                            *reinterpret_cast<float*>(gram + off) = hi;
-                            *reinterpret_cast<float*>(gram + A.lo_off + off) = cv - hi;
-                        } else {
-                            *reinterpret_cast<__nv_bfloat16*>(gram + off) = __float2bfloat16_rn(cv);
-                        }
-                    }
+                    if (TC) put_operand<GRAM>(gram, A, my_l, q, s, cv);
                 }
             }
         }
     }
     if (GRAM == kGramNone) return;
+    if (given_c) {  // operand tiles from the given coefficients of this centre
+        const float* cc = A.c_in + (int64_t)i * A.Q * A.n_lm;
+        for (int e = tid; e < A.Q * A.n_lm; e += blockDim.x) {
+            const int q = e / A.n_lm, lm = e - q * A.n_lm;
+            const int l = (int)sqrtf((float)lm);
+            put_operand<GRAM>(gram, A, l, q, lm - l * l, __ldg(cc + e));
+        }
+    }
 
     // ------------------------------------------------------------------------------------ fused power spectrum
     float* pout = A.ps + (int64_t)i * A.ps_stride;
@@ -580,14 +583,14 @@ static ExpArgs make_args(rascal_ctx* ctx, const rascal_system* sys, const int64_
     A.offsets = d_offsets;
     A.nbr_j = d_nbr_j;
     A.rij = reinterpret_cast<const float4*>(d_rij);
-    A.species = sys->d_species;
+    A.species = sys ? sys->d_species : nullptr;
     A.lut = ctx->d_lut;
     A.table = ctx->d_table;
     A.tasks = ctx->d_tasks;
     A.fmap = ctx->d_fmap;
     A.coeffs = d_coeffs;
     A.flags = ctx->d_flags;
-    A.N = sys->n_atoms;
+    A.N = sys ? sys->n_atoms : 0;
     A.n_max = ctx->n_max;
     A.l_max = ctx->l_max;
     A.S = ctx->n_species;
@@ -719,6 +722,19 @@ static int launch_expansion(rascal_ctx* ctx, const ExpArgs& A, int n_atoms, int 
     k_expansion<GRAM><<<n_atoms, threads, smem, ctx->stream>>>(A);
     RASCAL_LAUNCH_CHECK("k_expansion");
     return RASCAL_OK;
+}
+
+int power_spectrum_tc(rascal_ctx* ctx, int64_t n_centres, const float* d_coeffs, int precision, int layout, float* d_ps) {
+    ExpArgs A = make_args(ctx, nullptr, nullptr, nullptr, nullptr, nullptr);
+    A.N = (int)n_centres;
+    A.c_in = d_coeffs;
+    const int mode = precision == RASCAL_PS_TF32X3 ? kGramTf32x3 : kGramBf16;
+    size_t smem;
+    int threads;
+    int st = make_gram(ctx, mode, layout, d_ps, A, &smem, &threads);
+    if (st) return st;
+    return mode == kGramTf32x3 ? launch_expansion<kGramTf32x3>(ctx, A, (int)n_centres, threads, smem)
+                               : launch_expansion<kGramBf16>(ctx, A, (int)n_centres, threads, smem);
 }
 
 }  // namespace rascal

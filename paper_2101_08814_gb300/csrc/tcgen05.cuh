@@ -98,7 +98,6 @@ __device__ inline void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
-__device__ inline void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Bulk (non-tensor) asynchronous copy shared -> global by the issuing thread: both addresses 16-byte aligned,
 // size a multiple of 16 bytes. The writers of the source make their stores visible to the async proxy
