@@ -67,6 +67,9 @@ def parse_args(argv=None):
                     help="radial integrals from the FP32 spline, the per-pair FP64 1F1, or the MLP surrogate "
                          "(trained on the GPU before timing)")
     ap.add_argument("--mlp-steps", type=int, default=4000, help="Adam steps of the surrogate's training (setup)")
+    ap.add_argument("--select", type=float, default=0.0,
+                    help="fraction of the packed power-spectrum features to compute (seeded random selection; "
+                         "rascal_soap_selected); 0 = all")
     ap.add_argument("--expansion-only", action="store_true",
                     help="neighbours + coefficients only (rascal_spherical_expansion), no power spectrum")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
@@ -306,9 +309,20 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     Qc = calc.coeffs_per_centre
     Fp = calc.n_features(args.layout)
+    if args.gradients and args.select > 0:
+        raise SystemExit("--gradients uses the full packed power spectrum; it does not combine with --select")
     if args.gradients and args.layout != "packed":
         raise SystemExit("--gradients uses the linear model over the packed features (--layout packed)")
     coeffs = torch.empty((N, calc.n_species, calc.n_max, (calc.l_max + 1) ** 2), dtype=torch.float32, device=dev)
+    sel = None
+    if args.select > 0:
+        import numpy as np
+
+        Fpk = calc.n_features("packed")
+        n_sel = max(1, int(round(args.select * Fpk)))
+        sel = torch.tensor(np.sort(np.random.default_rng(11).choice(Fpk, n_sel, replace=False)).astype(np.int32),
+                           device=dev)
+        Fp = n_sel
     ps = torch.empty((N, Fp), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     radial_info = radial_setup(args, calc, system, dev, rg)
@@ -333,6 +347,9 @@ def run_ours(args):
             mark(2)
             if not args.expansion_only:
                 calc.power_spectrum(coeffs, precision=args.ps, layout=args.layout, out=ps)
+        elif sel is not None:
+            calc.soap_selected(ds, pairs, sel, coeffs=coeffs, ps=ps)
+            mark(2)
         else:
             calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps)
             mark(2)
@@ -407,7 +424,7 @@ def run_ours(args):
     else:
         achieved = (alg / (t_ms * 1e-3) / 1e9) if alg else None
         traffic_known = (kernel.startswith("k_expansion<fused") and args.config == "batch" and args.ps == "fp32"
-                         and args.layout == "packed" and args.radial == "spline")
+                         and args.layout == "packed" and args.radial == "spline" and sel is None)
         roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": (achieved / peak) if achieved else None,
                     "traffic": FUSED_FP32_TRAFFIC_PER_ENV * N if traffic_known else None,
@@ -418,7 +435,7 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e and world >= 1:
-        e2e = measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, weights=weights)
+        e2e = measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, weights=weights, sel=sel)
         e2e["ms"] = max_over_ranks(e2e["ms"], dev)
         e2e = {"value": total_env / (e2e["ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e["ms"]}
@@ -432,7 +449,8 @@ def run_ours(args):
             "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}", "global_batch": total_env,
                        "env_per_gpu": N, "pairs_per_gpu": n_pairs,
                        "power_spectrum": None if args.expansion_only else {"layout": args.layout, "precision": args.ps,
-                                                                          "fused": fused},
+                                                                          "fused": fused, "features": Fp,
+                                                                          "selected": sel is not None},
                        "gradients": bool(args.gradients), **radial_info,
                        "parallelism": f"dp{world} (independent batches per GPU)",
                        "l2": "256 MB buffer written before every timed step (L2 is 129 MB), outside the step events",
@@ -501,7 +519,7 @@ def coefficient_error(calc, ds, coeffs, rg, args):
     return {args.radial: err(mine, ref), "spline": err(spline, ref)}
 
 
-def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None, weights=None):
+def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None, weights=None, sel=None):
     """Same step through the public API with host buffers: pinned H2D of the inputs, D2H of the power spectrum.
 
     Steps are pipelined the way a streaming user would run them: the power spectrum of step k leaves on a copy
@@ -544,6 +562,8 @@ def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None, wei
         elif args.separate:
             calc.spherical_expansion(ds, pairs, out=coeffs)
             calc.power_spectrum(coeffs, precision=args.ps, layout=args.layout, out=ps_buf[b])
+        elif sel is not None:
+            calc.soap_selected(ds, pairs, sel, coeffs=coeffs, ps=ps_buf[b])
         else:
             calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps_buf[b])
         if weights is not None:

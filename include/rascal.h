@@ -175,6 +175,18 @@ int rascal_power_spectrum(rascal_ctx* ctx, int64_t n_centres, const float* d_coe
 int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,
                 const float* d_rij, int precision, int layout, float* d_coeffs, float* d_ps);
 
+/* Selected power-spectrum features (sparse feature selection, Sec. "Feature dimensionality reduction"): only the
+ * listed PACKED features are computed (FP32, in the fused kernel, from c held in shared memory) and written densely,
+ * so the output bytes, which bound the full power spectrum, shrink with the selection.
+ *   n_sel >= 1; d_sel [n_sel] int32: indices f = l Q(Q+1)/2 + q1 (2Q - q1 - 1)/2 + q2 (q1 <= q2) into the PACKED
+ *     feature vector of rascal_power_spectrum, any order, repeats allowed
+ *   d_coeffs [n_atoms][n_species][n_max][(l_max+1)^2] float32: written as by rascal_soap
+ *   d_ps [n_atoms][n_sel] float32: d_ps[i][k] = p^i at feature d_sel[k]
+ * An index outside [0, features_packed) is reported as RASCAL_E_ARG at the next synchronising call (its output is
+ * left zero). */
+int rascal_soap_selected(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,
+                         const float* d_rij, int64_t n_sel, const int* d_sel, float* d_coeffs, float* d_ps);
+
 /* Per-structure energy of the additive linear model E = sum_i w_{a_i} . p_i (Eq. additive-energy-model) from
  * PACKED p: d_weights [n_species][features_packed] float32, d_energy [n_structures] float64 (overwritten). */
 int rascal_linear_energy(rascal_ctx* ctx, const rascal_system* sys, const float* d_ps_packed,

@@ -180,6 +180,21 @@ class SoapCalculator:
                                           _ptr(pairs.rij), PRECISION[precision], LAYOUT[layout], _ptr(c), _ptr(p)))
         return c, p
 
+    def soap_selected(self, system: DeviceSystem, pairs: PairList, sel, coeffs=None, ps=None):
+        """c and the selected PACKED power-spectrum features ([N][len(sel)]) in one fused kernel launch."""
+        import torch
+
+        self._bind_stream()
+        N = system.n_atoms
+        sel = torch.as_tensor(sel, dtype=torch.int32, device=self.device).contiguous()
+        c = coeffs if coeffs is not None else torch.empty((N, self.n_species, self.n_max, (self.l_max + 1) ** 2),
+                                                          dtype=torch.float32, device=self.device)
+        p = ps if ps is not None else torch.empty((N, sel.numel()), dtype=torch.float32, device=self.device)
+        sys_c = system.c_struct()
+        _lib.check(_lib.lib().rascal_soap_selected(self._ctx, C.byref(sys_c), _ptr(pairs.offsets), _ptr(pairs.nbr_j),
+                                                   _ptr(pairs.rij), int(sel.numel()), _ptr(sel), _ptr(c), _ptr(p)))
+        return c, p
+
     def linear_energy(self, system: DeviceSystem, ps_packed, weights):
         import torch
 

@@ -93,6 +93,8 @@ _SIGNATURES = {
     "rascal_power_spectrum": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "rascal_soap": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                               C.c_void_p, C.c_void_p]),
+    "rascal_soap_selected": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]),
     "rascal_linear_energy": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p]),
     "rascal_gradients": (C.c_int, [C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -28,6 +28,7 @@ enum : unsigned {
     kFlagShiftRange = 1u << 3,  // |n_k| above kMaxShift
     kFlagBadOffsets = 1u << 4,  // structure offsets not increasing / out of range
     kFlagTimeout = 1u << 5,     // a bounded wait on a tensor-core completion barrier ran out
+    kFlagSelection = 1u << 6,   // a selected feature index is outside the packed feature vector
 };
 
 // -------------------------------------------------------------------------------------------- status
@@ -107,6 +108,7 @@ struct rascal_ctx {
     rascal::Arena scratch;  // grown on demand, reused across calls
     rascal::Arena scratch2;
     rascal::Arena scratch_w;  // dense symmetric weight blocks of the gradient kernel
+    rascal::Arena scratch_sel;  // decoded feature selection of rascal_soap_selected
     int64_t* h_pinned;      // pinned host words for small read-backs
 
     rascal::ExpPlan plan;

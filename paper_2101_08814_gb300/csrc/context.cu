@@ -61,6 +61,7 @@ int check_flags(rascal_ctx* ctx) {
     if (f & kFlagThinCell) return set_error(RASCAL_E_UNSUPPORTED, "a cell is thinner than r_cut/64 along some axis");
     if (f & kFlagShiftRange) return set_error(RASCAL_E_UNSUPPORTED, "a periodic shift exceeds |n| <= 511");
     if (f & kFlagTimeout) return set_error(RASCAL_E_TIMEOUT, "a bounded wait for tensor-core completion timed out");
+    if (f & kFlagSelection) return set_error(RASCAL_E_ARG, "a selected feature index is outside [0, features_packed)");
     return set_error(RASCAL_E_CUDA, "unknown device flag 0x%x", f);
 }
 
@@ -398,6 +399,7 @@ extern "C" void rascal_destroy(rascal_ctx* ctx) {
     cudaFreeHost(ctx->h_pinned);
     cudaFree(ctx->scratch.ptr);
     cudaFree(ctx->scratch_w.ptr);
+    cudaFree(ctx->scratch_sel.ptr);
     cudaFree(ctx->scratch2.ptr);
     delete ctx;
 }

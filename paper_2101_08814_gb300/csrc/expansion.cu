@@ -43,6 +43,8 @@ struct ExpArgs {
     const float4* table;
     const float* pre_G;  // per-pair radial values [P][F] (EXACT / MLP modes) or NULL (spline table)
     const float* c_in;   // tensor-core power spectrum of given coefficients [N][Q][n_lm]: no pair phase, or NULL
+    const int* sel;      // selected features (FP32 form): packed (l | q1 << 8 | q2 << 16) per output column, or NULL
+    int n_sel;
     const int* tasks;
     const int* fmap;
     float* coeffs;
@@ -388,6 +390,21 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     if (nq > 3) d[3 * n_lm] = v.w;
                 }
             }
+        }
+        if (A.sel) {  // selected features only: one dot product of length 2l+1 per output, coalesced stores
+            float* po = A.ps + (int64_t)i * A.n_sel;
+            for (int k = tid; k < A.n_sel; k += blockDim.x) {
+                const int packed = __ldg(A.sel + k);
+                const int l = packed & 0xff, q1 = (packed >> 8) & 0xff, q2 = (packed >> 16) & 0xff;
+                float acc = 0.0f;
+                if (l <= A.l_max) {
+                    const float* r = CT + l * l * A.Qp;
+                    for (int m = 0; m <= 2 * l; ++m, r += A.Qp) acc = fmaf(r[q1], r[q2], acc);
+                    if (A.ps_norm) acc *= rsqrtf((float)(2 * l + 1));
+                }
+                po[k] = acc;
+            }
+            return;
         }
         // groups of l alternate between two staging halves; each half is written again only after the bulk store
         // issued from it two groups earlier has finished reading it
@@ -753,6 +770,52 @@ extern "C" int rascal_spherical_expansion(rascal_ctx* ctx, const rascal_system* 
     const float* pre_D;
     if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, false, &A.pre_G, &pre_D))) return st;
     return launch_expansion<kGramNone>(ctx, A, sys->n_atoms, ctx->plan.threads, ctx->plan.smem);
+}
+
+// PACKED feature index -> (l | q1 << 8 | q2 << 16); out-of-range indices flag an error and decode to l = 255 (zero)
+__global__ void k_decode_sel(int64_t n_sel, const int* __restrict__ sel, int Q, int l_max, int* __restrict__ out,
+                             unsigned* flags) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n_sel) return;
+    const int per_l = Q * (Q + 1) / 2;
+    const int f = sel[k];
+    if (f < 0 || f >= (l_max + 1) * per_l) {
+        atomicOr(flags, kFlagSelection);
+        out[k] = 255;
+        return;
+    }
+    const int l = f / per_l, r = f - l * per_l;
+    int q1 = 0;  // row q1 starts at q1 (2Q - q1 + 1) / 2 (its diagonal entry)
+    while (q1 + 1 < Q && ((q1 + 1) * (2 * Q - q1)) / 2 <= r) ++q1;
+    const int q2 = r - (q1 * (2 * Q - q1 - 1)) / 2;
+    out[k] = l | (q1 << 8) | (q2 << 16);
+}
+
+extern "C" int rascal_soap_selected(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets,
+                                    const int* d_nbr_j, const float* d_rij, int64_t n_sel, const int* d_sel,
+                                    float* d_coeffs, float* d_ps) {
+    clear_error();
+    if (!ctx) return set_error(RASCAL_E_ARG, "NULL context");
+    int st = validate_system(ctx, sys);
+    if (st) return st;
+    if (n_sel < 1 || n_sel > 0x7fffffff) return set_error(RASCAL_E_ARG, "n_sel must be in [1, 2^31)");
+    if (sys->n_atoms == 0) return RASCAL_OK;
+    if (!d_offsets || !d_nbr_j || !d_rij || !d_sel || !d_coeffs || !d_ps) return set_error(RASCAL_E_ARG, "NULL device pointer");
+    if (ctx->Q > 255) return set_error(RASCAL_E_UNSUPPORTED, "feature selection needs n_species*n_max <= 255");
+    void* dec;
+    if ((st = arena_get(ctx->scratch_sel, sizeof(int) * (size_t)n_sel, &dec))) return st;
+    k_decode_sel<<<(unsigned)div_up(n_sel, 256), 256, 0, ctx->stream>>>(n_sel, d_sel, ctx->Q, ctx->l_max,
+                                                                       static_cast<int*>(dec), ctx->d_flags);
+    RASCAL_LAUNCH_CHECK("k_decode_sel");
+    ExpArgs A = make_args(ctx, sys, d_offsets, d_nbr_j, d_rij, d_coeffs);
+    const float* pre_D;
+    if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, false, &A.pre_G, &pre_D))) return st;
+    size_t smem;
+    int threads;
+    if ((st = make_gram(ctx, kGramSimt, RASCAL_LAYOUT_PACKED, d_ps, A, &smem, &threads))) return st;
+    A.sel = static_cast<const int*>(dec);
+    A.n_sel = (int)n_sel;
+    return launch_expansion<kGramSimt>(ctx, A, sys->n_atoms, threads, smem);
 }
 
 extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,
