@@ -223,14 +223,15 @@ struct MlpInferArgs {
 
 constexpr int kMlpH = 64;
 constexpr int kMlpTile = 128;
-constexpr uint32_t kMlpTmemCols = 512;
+// TMEM: values in columns 0..255, forward tangents (d/dr) in 256..511; without tangents two CTAs share an SM
+
 
 // offset of element (row, k) in a K-major no-swizzle bf16 tile with K = 64 (8 chunks of 16 bytes per 8-row group)
 __device__ __host__ inline int kmajor64_off(int row, int k) {
     return (row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-__global__ void __launch_bounds__(128, 1) k_mlp_infer(const MlpInferArgs A) {
+__global__ void __launch_bounds__(128, 2) k_mlp_infer(const MlpInferArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t s_bar;
     __shared__ uint32_t s_tmem;
@@ -238,10 +239,14 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer(const MlpInferArgs A) {
     unsigned char* w2 = smem;                              // 64 x 64 bf16 = 8 KB
     unsigned char* w3 = w2 + 8192;                         // F_pad x 64 bf16
     unsigned char* a1 = w3 + (size_t)A.F_pad * 128;        // 128 x 64 bf16 (h1), 16 KB
-    unsigned char* a1d = a1 + 16384;                       // tangent of h1
-    unsigned char* a2 = a1d + 16384;                       // h2
-    unsigned char* a2d = a2 + 16384;                       // tangent of h2
-    float* s_par = reinterpret_cast<float*>(a2d + 16384);  // W1, b1, b2 [H each], b3, scale [F each]
+    const bool deriv = A.dout != nullptr;
+    const uint32_t tm_cols = deriv ? 512u : 256u;
+    unsigned char* a1d = a1 + 16384;                       // tangent of h1 (only with derivatives)
+    unsigned char* a2 = a1d + (deriv ? 16384 : 0);         // h2
+    unsigned char* a2d = a2 + 16384;                       // tangent of h2 (only with derivatives)
+    float* s_par = reinterpret_cast<float*>(a2d + (deriv ? 16384 : 0));  // W1, b1, b2 [H each], b3, scale [F each]
+    // per-warp 32 x 16 output slabs (value and derivative, pitch 17): rows leave with coalesced stores
+    float* s_slab = s_par + ((3 * H + 2 * F + 3) & ~3) + (threadIdx.x >> 5) * 2 * 32 * 17;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // weights into shared memory (already laid out as operand tiles on the host side)
     for (int b = tid; b < 8192 / 16; b += blockDim.x) reinterpret_cast<uint4*>(w2)[b] = reinterpret_cast<const uint4*>(A.W2t)[b];
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer(const MlpInferArgs A) {
         s_par[3 * H + F + f] = A.scale[f];
     }
     if (warp == 0) {
-        tmem_alloc(&s_tmem, kMlpTmemCols);
+        tmem_alloc(&s_tmem, tm_cols);
         tmem_relinquish();
     }
     if (tid == 0) {
@@ -268,7 +273,6 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer(const MlpInferArgs A) {
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = s_tmem;
-    const bool deriv = A.dout != nullptr;
     const uint32_t id2 = instr_desc(1u, 128u, (uint32_t)H);
     const uint32_t id3 = instr_desc(1u, 128u, (uint32_t)A.F_pad);
     const uint32_t s_w2 = smem_u32(w2), s_w3 = smem_u32(w3), s_a1 = smem_u32(a1), s_a1d = smem_u32(a1d),
@@ -339,21 +343,31 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer(const MlpInferArgs A) {
         phase ^= 1u;
         if (!ok) break;
         tc_fence_after();
+        const int64_t row0 = tile * kMlpTile + 32 * warp;  // this warp's 32 rows (pairs)
         for (int c0 = 0; c0 < A.F_pad; c0 += 16) {
             float y[16], dy[16];
             tmem_ld16(taddr + lane_base + (uint32_t)c0, y);
             if (deriv) tmem_ld16(taddr + lane_base + 256u + (uint32_t)c0, dy);
-            if (valid) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int f = c0 + u;
-                    if (f < F) {
-                        const float sc = s_par[3 * H + F + f];
-                        A.out[p * F + f] = sc * (y[u] + s_par[3 * H + f]);
-                        if (deriv) A.dout[p * F + f] = sc * dy[u];
-                    }
+            for (int u = 0; u < 16; ++u) {
+                const int f = min(c0 + u, F - 1);
+                const float sc = s_par[3 * H + F + f];
+                s_slab[lane * 17 + u] = sc * (y[u] + s_par[3 * H + f]);
+                if (deriv) s_slab[32 * 17 + lane * 17 + u] = sc * dy[u];
+            }
+            __syncwarp();
+            // two rows per store instruction: lanes 0..15 row 2k, lanes 16..31 row 2k+1, 16 consecutive columns
+            const int cc = lane & 15, f = c0 + cc;
+#pragma unroll 4
+            for (int k = 0; k < 16; ++k) {
+                const int rr = 2 * k + (lane >> 4);
+                const int64_t pr = row0 + rr;
+                if (pr < A.n && f < F) {
+                    A.out[pr * F + f] = s_slab[rr * 17 + cc];
+                    if (deriv) A.dout[pr * F + f] = s_slab[32 * 17 + rr * 17 + cc];
                 }
             }
+            __syncwarp();
         }
         tc_fence_before();
         __syncthreads();
@@ -364,7 +378,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer(const MlpInferArgs A) {
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(taddr, kMlpTmemCols);
+        tmem_dealloc(taddr, tm_cols);
     }
     (void)lane;
 }
@@ -426,9 +440,11 @@ int mlp_infer(rascal_ctx* ctx, int64_t n, const float4* rij, const float* r, flo
     A.F_pad = F_pad;
     A.inv_rscale = (float)(1.0 / ctx->r_cut);
     A.flags = ctx->d_flags;
-    const size_t smem = 8192 + (size_t)F_pad * 128 + 4 * 16384 + sizeof(float) * (3 * kMlpH + 2 * ctx->F) + 64;
+    const size_t smem = 8192 + (size_t)F_pad * 128 + (dout ? 4 : 2) * 16384 +
+                        sizeof(float) * ((3 * kMlpH + 2 * ctx->F + 3) / 4 * 4 + 4 * 2 * 32 * 17) + 64;
     const int64_t tiles = (n + kMlpTile - 1) / kMlpTile;
-    const unsigned grid = (unsigned)std::min<int64_t>(tiles, ctx->n_sm);
+    // one CTA per SM with tangents (all 512 TMEM columns), two without
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)ctx->n_sm * (dout ? 1 : 2));
     k_mlp_infer<<<grid, 128, smem, ctx->stream>>>(A);
     RASCAL_LAUNCH_CHECK("k_mlp_infer");
     return RASCAL_OK;
