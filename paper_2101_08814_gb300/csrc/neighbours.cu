@@ -35,8 +35,8 @@ struct StructInfo {
 };
 
 constexpr int kPairWarps = 4;     // warps per block in k_pairs
-constexpr int kPairCap = 256;     // pairs a warp sorts in shared memory; larger segments use global scratch
-constexpr int kPairEPL = kPairCap / 32;
+constexpr int kPairCap = 128;     // pairs a warp sorts in shared memory; larger segments use global scratch
+constexpr int kNoallocCap = 256;  // the same for rascal_neighbours_noalloc, which has no overflow scratch
 
 __device__ inline int floordiv(int a, int b) {
     const int q = a / b;
@@ -243,16 +243,18 @@ __device__ inline uint64_t pair_key(int j, const int n[3]) {
            (uint64_t)(n[2] + 512);
 }
 
-template <bool FILL>
-__global__ void __launch_bounds__(kPairWarps * 32) k_pairs(
+// CAP: pairs a warp sorts in shared memory (8 blocks of 4 warps per SM at CAP = 128)
+template <bool FILL, int CAP = kPairCap>
+__global__ void __launch_bounds__(kPairWarps * 32, CAP <= 128 ? 8 : 0) k_pairs(
     int n_atoms, const double* __restrict__ pos, const StructInfo* __restrict__ info, const int64_t* __restrict__ binbase,
     const int64_t* __restrict__ bin_start, const float4* __restrict__ sorted_hi, const int* __restrict__ atom_struct,
     const int4* __restrict__ atom_cell, const int4* __restrict__ atom_wrap, const float4* __restrict__ atom_hi,
     const float4* __restrict__ atom_lo, double rc2, int64_t nbins_cap, int64_t* __restrict__ counts_or_offsets, int* __restrict__ max_count,
     int* __restrict__ out_j, int* __restrict__ out_shift, float4* __restrict__ out_rij, uint64_t* __restrict__ ovf_keys,
     float4* __restrict__ ovf_vec, unsigned* flags) {
-    __shared__ uint64_t s_keys[FILL ? kPairWarps * kPairCap : 1];
-    __shared__ float4 s_vec[FILL ? kPairWarps * kPairCap : 1];
+    constexpr int kPairEPL = CAP / 32;
+    __shared__ uint64_t s_keys[FILL ? kPairWarps * CAP : 1];
+    __shared__ float4 s_vec[FILL ? kPairWarps * CAP : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kPairWarps + warp;
     if (i >= n_atoms) return;
@@ -265,13 +267,13 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pairs(
     const float thr_lo2 = S.thr_lo2, thr_hi2 = S.thr_hi2, thr_tiny2 = S.thr_tiny2;
     const int bci[3] = {cell.x, cell.y, cell.z};
     int64_t seg_beg = 0, seg_cnt = 0;
-    uint64_t* keys = s_keys + warp * kPairCap;
-    float4* vecs = s_vec + warp * kPairCap;
+    uint64_t* keys = s_keys + warp * CAP;
+    float4* vecs = s_vec + warp * CAP;
     bool use_global = false;
     if (FILL) {
         seg_beg = counts_or_offsets[i];
         seg_cnt = counts_or_offsets[i + 1] - seg_beg;
-        if (seg_cnt > kPairCap) {
+        if (seg_cnt > CAP) {
             use_global = true;
             keys = ovf_keys + seg_beg;
             vecs = ovf_vec + seg_beg;
@@ -674,7 +676,7 @@ extern "C" int rascal_neighbours_noalloc(rascal_ctx* ctx, const rascal_system* s
     RASCAL_LAUNCH_CHECK("k_struct_thresholds");
     const double rc2 = ctx->r_cut * ctx->r_cut;
     const unsigned pair_blocks = (unsigned)div_up(N, kPairWarps);
-    k_pairs<false><<<pair_blocks, kPairWarps * 32, 0, stream>>>(N, sys->d_positions, info, binbase, bin_start, sorted_hi,
+    k_pairs<false, kNoallocCap><<<pair_blocks, kPairWarps * 32, 0, stream>>>(N, sys->d_positions, info, binbase, bin_start, sorted_hi,
                                                                 atom_struct, atom_cell, atom_wrap, atom_hi, atom_lo, rc2,
                                                                 nbins_cap, d_offsets, max_count, nullptr, nullptr, nullptr,
                                                                 nullptr, nullptr, ctx->d_flags);
@@ -689,10 +691,10 @@ extern "C" int rascal_neighbours_noalloc(rascal_ctx* ctx, const rascal_system* s
     if (P > capacity) return set_error(RASCAL_E_CAPACITY, "pair capacity %lld < required %lld", (long long)capacity, (long long)P);
     if (P == 0) return RASCAL_OK;
     if (!d_nbr_j || !d_shift || !d_rij) return set_error(RASCAL_E_ARG, "NULL pair output arrays");
-    if (maxc > kPairCap)
+    if (maxc > kNoallocCap)
         return set_error(RASCAL_E_UNSUPPORTED, "a centre has %d neighbours; the no-allocation entry point sorts at most %d "
-                         "per centre (rascal_neighbours has no such limit)", maxc, kPairCap);
-    k_pairs<true><<<pair_blocks, kPairWarps * 32, 0, stream>>>(N, sys->d_positions, info, binbase, bin_start, sorted_hi,
+                         "per centre (rascal_neighbours has no such limit)", maxc, kNoallocCap);
+    k_pairs<true, kNoallocCap><<<pair_blocks, kPairWarps * 32, 0, stream>>>(N, sys->d_positions, info, binbase, bin_start, sorted_hi,
                                                                atom_struct, atom_cell, atom_wrap, atom_hi, atom_lo, rc2,
                                                                nbins_cap, d_offsets, nullptr, d_nbr_j, d_shift,
                                                                reinterpret_cast<float4*>(d_rij), nullptr, nullptr,
