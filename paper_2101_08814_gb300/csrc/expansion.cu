@@ -31,7 +31,9 @@
 
 namespace rascal {
 
-enum GramMode : int { kGramNone = 0, kGramSimt = 1, kGramBf16 = 2, kGramTf32x3 = 3 };
+// kGramSel: the FP32 form restricted to listed features (its own instantiation, so that the full Gram's register
+// allocation is not affected by the selection branch)
+enum GramMode : int { kGramNone = 0, kGramSimt = 1, kGramBf16 = 2, kGramTf32x3 = 3, kGramSel = 4 };
 constexpr int kMaxGroups = kMaxLMax + 2;
 
 struct ExpArgs {
@@ -132,7 +134,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
     if (tid < kMaxLMax + 2) s_lp[tid] = A.lp[tid];
     #pragma unroll 1
     for (int t = tid; t < A.F_pad; t += blockDim.x) s_fmap[t] = A.fmap[t];
-    if (GRAM == kGramSimt) {  // columns Q..ceil4(Q)-1 of CT are read by the edge tiles and must be zero
+    constexpr bool kCT = (GRAM == kGramSimt || GRAM == kGramSel);  // c held transposed in shared memory
+    if (kCT) {  // columns Q..ceil4(Q)-1 of CT are read by the edge tiles and must be zero
         float* CT = reinterpret_cast<float*>(gram);
         const int q_end = (A.Q + 3) & ~3;
         if (q_end > A.Q)
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     }
                 }
             }
-            if (GRAM == kGramSimt) {  // tile -> CT[l^2 + s][a n_max + n]; c reaches HBM from CT afterwards
+            if (kCT) {  // tile -> CT[l^2 + s][a n_max + n]; c reaches HBM from CT afterwards
                 float* ct = reinterpret_cast<float*>(gram) + (my_l * my_l + 4 * my_mt) * A.Qp + a * A.n_max + 4 * my_nt;
                 const int v_end = 2 * my_l + 1 - 4 * my_mt, u_end = A.n_max - 4 * my_nt;
                 const bool vec = u_end >= 4 && (A.n_max & 3) == 0;
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
 
     // ------------------------------------------------------------------------------------ fused power spectrum
     float* pout = A.ps + (int64_t)i * A.ps_stride;
-    if (GRAM == kGramSimt) {
+    if (kCT) {
         fence_proxy_async_smem();
         __syncthreads();
         const float* CT = reinterpret_cast<const float*>(gram);
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 }
             }
         }
-        if (A.sel) {  // selected features only: one dot product of length 2l+1 per output, coalesced stores
+        if (GRAM == kGramSel) {  // selected features only: one dot product of length 2l+1 per output, coalesced stores
             float* po = A.ps + (int64_t)i * A.n_sel;
             for (int k = tid; k < A.n_sel; k += blockDim.x) {
                 const int packed = __ldg(A.sel + k);
@@ -585,7 +588,8 @@ int expansion_setup(rascal_ctx* ctx) {
     RASCAL_CUDA(cudaMemcpyAsync(ctx->d_fmap, fmap.data(), sizeof(int) * fmap.size(), cudaMemcpyHostToDevice, ctx->stream));
     RASCAL_CUDA(upload_ylm_constants(ctx->stream));
     int st;
-    if ((st = set_attr<kGramNone>()) || (st = set_attr<kGramSimt>()) || (st = set_attr<kGramBf16>()) ||
+    if ((st = set_attr<kGramNone>()) || (st = set_attr<kGramSimt>()) || (st = set_attr<kGramSel>()) ||
+        (st = set_attr<kGramBf16>()) ||
         (st = set_attr<kGramTf32x3>()))
         return st;
     RASCAL_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -815,7 +819,7 @@ extern "C" int rascal_soap_selected(rascal_ctx* ctx, const rascal_system* sys, c
     if ((st = make_gram(ctx, kGramSimt, RASCAL_LAYOUT_PACKED, d_ps, A, &smem, &threads))) return st;
     A.sel = static_cast<const int*>(dec);
     A.n_sel = (int)n_sel;
-    return launch_expansion<kGramSimt>(ctx, A, sys->n_atoms, threads, smem);
+    return launch_expansion<kGramSel>(ctx, A, sys->n_atoms, threads, smem);
 }
 
 extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,
