@@ -132,7 +132,7 @@ __global__ void k_wsym(int S, int L1, int Q, int Qw, int ps_norm, const float* _
 //      contraction s = sum_lm Y sum_n chat (f I)', w = sum_lm dY/du sum_n chat f I (one warp per pair, lanes over
 //      lm, warp-shuffle reduction);
 //      dE/dr_ji, the force scatter and the virial (one thread per pair).
-__global__ void __launch_bounds__(kGradThreads) k_gradients(const GradArgs A) {
+__global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int chunk = A.chunk;
     const int QN = A.Q * A.n_lm;
@@ -550,9 +550,9 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
         for (int l = L1; l < kMaxLMax + 1; ++l) A.adj_pref[l + 1] = A.adj_pref[l];
         A.n_adj_tasks = A.adj_pref[L1];
     }
-    // the largest chunk (<= 32: warp 0 runs the per-pair phase) that keeps four CTAs per SM
+    // the largest chunk (<= 32: warp 0 runs the per-pair phase) that keeps five CTAs per SM (48 registers)
     int chunk = 32;
-    while (chunk > 1 && grad_smem(ctx, chunk, A.wsym != nullptr) > 56 * 1024) --chunk;
+    while (chunk > 1 && grad_smem(ctx, chunk, A.wsym != nullptr) > 44 * 1024) --chunk;
     A.chunk = chunk;
     A.aux_off = (int)grad_aux_off(ctx, chunk, A.wsym != nullptr);
     const size_t smem = grad_smem(ctx, chunk, A.wsym != nullptr);
