@@ -23,13 +23,13 @@ from math import pi, sqrt
 
 import numpy as np
 
-from . import radial, ylm
+from . import dvr, radial, ylm
 from .neighbours import neighbour_list
 
 
 class Hypers:
     def __init__(self, r_cut, sigma, n_max, l_max, species, smooth_width=0.5, orthonormal=True, include_center=False,
-                 ps_norm=True, **_ignored):
+                 ps_norm=True, basis="gto", **_ignored):
         self.r_cut = float(r_cut)
         self.sigma = float(sigma)
         self.n_max = int(n_max)
@@ -39,6 +39,7 @@ class Hypers:
         self.orthonormal = bool(orthonormal)
         self.include_center = bool(include_center)
         self.ps_norm = bool(ps_norm)
+        self.basis = str(basis)  # "gto" (Eq. rad-int-gto-1, o-GTO unless orthonormal is off) or "dvr" (Eq. rad-int-dvr)
 
     @property
     def n_species(self):
@@ -75,6 +76,8 @@ def cutoff(r, r_cut, width, derivative=False):
 def _radial(r, h: Hypers, derivative=False, radial_fn=None):
     if radial_fn is not None:
         return radial_fn(r, derivative)
+    if h.basis == "dvr":
+        return dvr.integrals(r, h.r_cut, h.sigma, h.n_max, h.l_max, derivative)
     return radial.integrals(r, h.r_cut, h.sigma, h.n_max, h.l_max, h.orthonormal, derivative)
 
 
