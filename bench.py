@@ -66,6 +66,8 @@ def parse_args(argv=None):
     ap.add_argument("--radial", choices=["spline", "exact", "mlp"], default="spline",
                     help="radial integrals from the FP32 spline, the per-pair FP64 1F1, or the MLP surrogate "
                          "(trained on the GPU before timing)")
+    ap.add_argument("--basis", choices=["gto", "dvr"], default="gto",
+                    help="radial basis: GTO (Eq. rad-int-gto-1, orthonormalised) or DVR (Eq. rad-int-dvr)")
     ap.add_argument("--mlp-steps", type=int, default=4000, help="Adam steps of the surrogate's training (setup)")
     ap.add_argument("--select", type=float, default=0.0,
                     help="fraction of the packed power-spectrum features to compute (seeded random selection; "
@@ -183,6 +185,7 @@ def cpu_worker(args):
     from oracle import soap as osoap
 
     system = make_system(args.config, 0)
+    system.hypers = dict(system.hypers, basis=args.basis)
     h = osoap.Hypers(**system.hypers)
     rng = np.random.default_rng(123)
     order = rng.permutation(system.n_atoms)
@@ -217,14 +220,14 @@ def cpu_baseline(args, cores=1):
     env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores),
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--config", args.config, "--layout", args.layout,
-           "--cpu-seconds", str(args.cpu_seconds)] + (["--gradients"] if args.gradients else []) + \
+           "--cpu-seconds", str(args.cpu_seconds), "--basis", args.basis] + (["--gradients"] if args.gradients else []) + \
           (["--expansion-only"] if args.expansion_only else [])
     res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     if res.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": res.stderr[-300:]}
     d = json.loads(res.stdout.strip().splitlines()[-1])
     return {"value": d["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{d['n']} seeded random centres of the {args.config} workload (neighbours + exact-1F1 coefficients"
+            "sample": f"{d['n']} seeded random centres of the {args.config} workload (neighbours + exact {'1F1' if args.basis == 'gto' else 'DVR'} coefficients"
                       f"{'' if args.expansion_only else ' + ' + args.layout + ' power spectrum'}"
                       f"{' + forces and virial' if args.gradients else ''}, FP64 numpy), "
                       f"{d['seconds']:.1f} s on one host thread"}
@@ -239,6 +242,7 @@ def run_reference(args):
     from oracle import soap as osoap
 
     system = make_system(args.config, 0)
+    system.hypers = dict(system.hypers, basis=args.basis)
     h = osoap.Hypers(**system.hypers)
     rng = np.random.default_rng(7)
     order = rng.permutation(system.n_atoms)
@@ -275,8 +279,8 @@ def run_reference(args):
         step()
     dt = time.perf_counter() - t0
     value = per_step * args.steps / dt
-    sample = (f"{per_step} seeded random centres per step of the {args.config} workload (neighbours + exact-1F1 "
-              f"coefficients{'' if args.expansion_only else ' + ' + args.layout + ' power spectrum'}"
+    sample = (f"{per_step} seeded random centres per step of the {args.config} workload (neighbours + exact "
+              f"{'1F1' if args.basis == 'gto' else 'DVR'} coefficients{'' if args.expansion_only else ' + ' + args.layout + ' power spectrum'}"
               f"{' + forces and virial' if args.gradients else ''}, "
               f"FP64 numpy), one host thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
@@ -303,6 +307,7 @@ def run_ours(args):
     import paper_2101_08814_gb300 as rg
 
     system = make_system(args.config, rank, args.structures)
+    system.hypers = dict(system.hypers, basis=args.basis)
     calc = rg.SoapCalculator(**system.hypers, device=dev)
     ds = rg.DeviceSystem.from_numpy(system, device=dev)
     N = ds.n_atoms
@@ -451,7 +456,7 @@ def run_ours(args):
                        "power_spectrum": None if args.expansion_only else {"layout": args.layout, "precision": args.ps,
                                                                           "fused": fused, "features": Fp,
                                                                           "selected": sel is not None},
-                       "gradients": bool(args.gradients), **radial_info,
+                       "gradients": bool(args.gradients), "radial_basis": args.basis, **radial_info,
                        "parallelism": f"dp{world} (independent batches per GPU)",
                        "l2": "256 MB buffer written before every timed step (L2 is 129 MB), outside the step events",
                        "stage_ms": {"neighbours": mean[0], ("expansion" if not fused else "soap"): mean[1],

@@ -57,6 +57,10 @@ extern "C" {
 #define RASCAL_PS_TF32X3 2 /* FP32 inputs split into TF32 hi + lo, three tcgen05 MMAs, FP32 accumulation:
                               about 2^-21 relative per product, FP32-grade results on tensor cores */
 
+/* radial basis */
+#define RASCAL_BASIS_GTO 0 /* Gaussian-type orbitals, Eq. rad-int-gto-1 (orthonormalised unless orthonormal = 0) */
+#define RASCAL_BASIS_DVR 1 /* discrete variable representation on Gauss-Legendre points, Eq. rad-int-dvr */
+
 /* power-spectrum layout */
 #define RASCAL_LAYOUT_PACKED 0
 #define RASCAL_LAYOUT_FULL 1
@@ -77,6 +81,10 @@ typedef struct {
     int ps_norm;             /* 1: keep the (2l+1)^-1/2 factor of Eq. nu2-basis-coupled */
     double spline_accuracy;  /* target max |spline - exact| at interval midpoints (FP64 build); <= 0: 1e-8 */
     int spline_intervals;    /* > 0: force this many intervals M; 0: double M from 64 until the accuracy holds */
+    int radial_basis;        /* RASCAL_BASIS_GTO or RASCAL_BASIS_DVR. DVR: I_nl(r) = 4 pi x_n sqrt(w_n)
+                              * exp(-a (x_n^2 + r^2)) i_l(2 a x_n r), a = 1/(2 sigma^2), on the n_max Gauss-Legendre
+                              * points x_n (weights w_n) of [0, r_cut + 3 sigma]; the printed Eq. rad-int-dvr leaves
+                              * out the constant 4 pi and the density factor exp(-a r^2), both kept here */
 } rascal_hypers;
 
 /* Structures in device memory. Atoms of structure s are struct_offsets[s] .. struct_offsets[s+1]-1. */

@@ -74,7 +74,8 @@ class SoapCalculator:
     """Owns one library context (radial spline table and scratch) for a set of hypers."""
 
     def __init__(self, r_cut, sigma, n_max, l_max, species, smooth_width=0.5, radial="spline", orthonormal=True,
-                 include_center=False, ps_norm=True, spline_accuracy=0.0, spline_intervals=0, device=None, **_ignored):
+                 include_center=False, ps_norm=True, spline_accuracy=0.0, spline_intervals=0, basis="gto", device=None,
+                 **_ignored):
         import torch
 
         self.device = torch.device("cuda" if device is None else device)
@@ -83,7 +84,7 @@ class SoapCalculator:
         self._species_arr = arr
         h = _lib.Hypers(float(r_cut), float(smooth_width), float(sigma), int(n_max), int(l_max), len(self.species),
                         C.cast(arr, C.POINTER(C.c_int)), RADIAL[radial], int(bool(orthonormal)), int(bool(include_center)),
-                        int(bool(ps_norm)), float(spline_accuracy), int(spline_intervals))
+                        int(bool(ps_norm)), float(spline_accuracy), int(spline_intervals), _lib.BASIS[basis])
         self._ctx = C.c_void_p()
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream().cuda_stream

@@ -19,6 +19,7 @@ RASCAL_E_NOMEM = -7
 RADIAL = {"spline": 0, "exact": 1, "mlp": 2}
 PRECISION = {"fp32": 0, "bf16": 1, "tf32x3": 2}
 LAYOUT = {"packed": 0, "full": 1}
+BASIS = {"gto": 0, "dvr": 1}
 
 
 class Hypers(C.Structure):
@@ -36,6 +37,7 @@ class Hypers(C.Structure):
         ("ps_norm", C.c_int),
         ("spline_accuracy", C.c_double),
         ("spline_intervals", C.c_int),
+        ("radial_basis", C.c_int),
     ]
 
 

@@ -100,6 +100,8 @@ struct rascal_ctx {
     double* d_T;        // [n_max][n_max] S^-1/2 (identity when orthonormal == 0)
     double* d_gto;      // [3][n_max+1]: d_n, N_n, (unused) for n = 0..n_max
     double* d_switch;   // [(n_max+1)][(l_max+2)] series/asymptotic switch points of G(a,b)
+    int basis;          // RASCAL_BASIS_GTO or RASCAL_BASIS_DVR
+    double* d_dvr;      // [2][n_max]: Gauss-Legendre points x_n and weights w_n on [0, r_cut + 3 sigma] (DVR basis)
     int* d_lut;         // [256] label -> species index or -1
 
     unsigned* d_flags;  // device error flags (see kFlag*)

@@ -293,11 +293,65 @@ __global__ void k_fill_grid(int64_t n, double step, double offset, double* r) {
     if (i < n) r[i] = offset + step * i;
 }
 
+// Exact FP64 DVR integrals and r-derivatives at n_pts distances: one thread per (point, n); layout as k_radial_fp64.
+__global__ void k_radial_dvr_fp64(int64_t n_pts, const double* __restrict__ r_in, int n_max, int l_max, double a,
+                                  const double* __restrict__ dvr, double* __restrict__ out, double* __restrict__ dout) {
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= n_pts * n_max) return;
+    const int64_t pt = id / n_max;
+    const int n = (int)(id % n_max);
+    const int L1 = l_max + 1;
+    double I[kMaxLMax + 1], dI[kMaxLMax + 1];
+    dvr_radial(l_max, a, dvr[n], dvr[n_max + n], r_in[pt], I, dout ? dI : nullptr);
+    for (int l = 0; l < L1; ++l) {
+        out[(pt * n_max + n) * L1 + l] = I[l];
+        if (dout) dout[(pt * n_max + n) * L1 + l] = dI[l];
+    }
+}
+
+// Gauss-Legendre points and weights on [0, X] (host, FP64): Newton iterations on the Legendre polynomial P_n,
+// evaluated by its three-term recurrence, from the cosine estimates of the roots.
+static void gauss_legendre(int n, double X, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double t = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;  // P_0, P_1
+            for (int k = 1; k < n; ++k) {
+                const double p2 = ((2.0 * k + 1.0) * t * p1 - k * p0) / (k + 1.0);
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pn = (n == 0) ? 1.0 : p1, pm = (n == 1) ? 1.0 : p0;  // P_n, P_{n-1}
+            dp = n * (t * pn - pm) / (t * t - 1.0);
+            const double dt = pn / dp;
+            t -= dt;
+            if (fabs(dt) < 1e-16) break;
+        }
+        // recompute P_n'(t) at the converged root for the weight
+        double p0 = 1.0, p1 = t;
+        for (int k = 1; k < n; ++k) {
+            const double p2 = ((2.0 * k + 1.0) * t * p1 - k * p0) / (k + 1.0);
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (t * p1 - (n == 1 ? 1.0 : p0)) / (t * t - 1.0);
+        x[n - 1 - i] = 0.5 * X * (t + 1.0);  // ascending
+        w[n - 1 - i] = 0.5 * X * 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
 static int launch_radial_fp64(rascal_ctx* ctx, int64_t n_pts, const double* d_r, double* out, double* dout) {
     const int L1 = ctx->l_max + 1;
     const int64_t threads = n_pts * L1;
     if (threads == 0) return RASCAL_OK;
     const double c = 1.0 / (2.0 * ctx->sigma * ctx->sigma);
+    if (ctx->basis == RASCAL_BASIS_DVR) {
+        const int64_t nt = n_pts * ctx->n_max;
+        k_radial_dvr_fp64<<<(unsigned)div_up(nt, 128), 128, 0, ctx->stream>>>(n_pts, d_r, ctx->n_max, ctx->l_max, c,
+                                                                             ctx->d_dvr, out, dout);
+        RASCAL_LAUNCH_CHECK("k_radial_dvr_fp64");
+        return RASCAL_OK;
+    }
     k_radial_fp64<<<(unsigned)div_up(threads, 128), 128, 0, ctx->stream>>>(n_pts, d_r, ctx->n_max, ctx->l_max, c, ctx->d_gto,
                                                                           ctx->d_T, ctx->d_switch, out, dout);
     RASCAL_LAUNCH_CHECK("k_radial_fp64");
@@ -399,6 +453,7 @@ extern "C" void rascal_destroy(rascal_ctx* ctx) {
     cudaFreeHost(ctx->h_pinned);
     cudaFree(ctx->scratch.ptr);
     cudaFree(ctx->scratch_w.ptr);
+    cudaFree(ctx->d_dvr);
     cudaFree(ctx->scratch_sel.ptr);
     cudaFree(ctx->scratch2.ptr);
     delete ctx;
@@ -416,6 +471,8 @@ static int create_impl(const rascal_hypers* h, void* stream, rascal_ctx** out) {
         return set_error(RASCAL_E_ARG, "n_species must be in [1, %d] with a species list", kMaxSpecies);
     if (h->n_species * h->n_max > kMaxQ) return set_error(RASCAL_E_ARG, "n_species*n_max must be <= %d", kMaxQ);
     if (h->radial < 0 || h->radial > 2) return set_error(RASCAL_E_ARG, "unknown radial mode %d", h->radial);
+    if (h->radial_basis != RASCAL_BASIS_GTO && h->radial_basis != RASCAL_BASIS_DVR)
+        return set_error(RASCAL_E_ARG, "unknown radial basis %d", h->radial_basis);
     std::vector<int> sp(h->species, h->species + h->n_species);
     std::sort(sp.begin(), sp.end());
     for (int i = 0; i < h->n_species; ++i) {
@@ -437,6 +494,7 @@ static int create_impl(const rascal_hypers* h, void* stream, rascal_ctx** out) {
     ctx->n_species = h->n_species;
     ctx->radial = h->radial;
     ctx->orthonormal = h->orthonormal ? 1 : 0;
+    ctx->basis = h->radial_basis;
     ctx->include_center = h->include_center ? 1 : 0;
     ctx->ps_norm = h->ps_norm ? 1 : 0;
     for (int i = 0; i < h->n_species; ++i) ctx->species[i] = sp[i];
@@ -453,6 +511,12 @@ static int create_impl(const rascal_hypers* h, void* stream, rascal_ctx** out) {
     RASCAL_CUDA(cudaMalloc(&ctx->d_gto, sizeof(double) * 3 * (n_max + 1)));
     RASCAL_CUDA(cudaMalloc(&ctx->d_T, sizeof(double) * n_max * n_max));
     RASCAL_CUDA(cudaMalloc(&ctx->d_switch, sizeof(double) * (n_max + 1) * L2));
+    if (ctx->basis == RASCAL_BASIS_DVR) {
+        std::vector<double> xw(2 * n_max);
+        gauss_legendre(n_max, h->r_cut + 3.0 * h->sigma, xw.data(), xw.data() + n_max);
+        RASCAL_CUDA(cudaMalloc(&ctx->d_dvr, sizeof(double) * 2 * n_max));
+        RASCAL_CUDA(cudaMemcpy(ctx->d_dvr, xw.data(), sizeof(double) * 2 * n_max, cudaMemcpyHostToDevice));
+    }
     RASCAL_CUDA(cudaMalloc(&ctx->d_lut, sizeof(int) * 256));
     RASCAL_CUDA(cudaMalloc(&ctx->d_flags, sizeof(unsigned)));
     RASCAL_CUDA(cudaMallocHost(&ctx->h_flags, sizeof(unsigned)));

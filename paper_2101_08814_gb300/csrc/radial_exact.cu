@@ -1,5 +1,5 @@
-// The radial integrals evaluated per pair from the 1F1 closed form, without spline or network (radial mode EXACT):
-// Eq. rad-int-gto-1 with the restricted 1F1 G(a, b, r) of Appendix A, followed by the o-GTO transform S^-1/2.
+// The radial integrals evaluated per pair from their closed forms, without spline or network (radial mode EXACT).
+// GTO basis: Eq. rad-int-gto-1 with the restricted 1F1 G(a, b, r) of Appendix A, followed by the o-GTO transform S^-1/2.
 //
 // For each pair and radial index n, four G values are evaluated directly (series below the switch point, asymptotic
 // series above): the main values M_l = G(a_l, b_l) and the auxiliary values X_l = G(a_l + 1, b_l + 1) at
@@ -73,6 +73,23 @@ __global__ void k_exact_mix(int64_t np, int n_max, int l_max, const double* __re
     }
 }
 
+// DVR integrals per (pair, n) in FP64 (Eq. rad-int-dvr; the basis is orthonormal, no transform follows), rounded to
+// FP32 in the [pair][l][n] layout.
+__global__ void k_exact_dvr(int64_t np, const float4* __restrict__ rij, int n_max, int l_max, double a,
+                            const double* __restrict__ dvr, float* __restrict__ out, float* __restrict__ dout) {
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= np * n_max) return;
+    const int64_t p = id / n_max;
+    const int n = (int)(id % n_max);
+    const int F = n_max * (l_max + 1);
+    double I[kMaxLMax + 1], dI[kMaxLMax + 1];
+    dvr_radial(l_max, a, dvr[n], dvr[n_max + n], (double)rij[p].w, I, dout ? dI : nullptr);
+    for (int l = 0; l <= l_max; ++l) {
+        out[p * F + l * n_max + n] = (float)I[l];
+        if (dout) dout[p * F + l * n_max + n] = (float)dI[l];
+    }
+}
+
 // Per-pair radial values for the EXACT and MLP radial modes, computed before the pair kernels run (the SPLINE mode
 // evaluates its table inside them and leaves *pre_G = NULL). Reads the pair count from the device (one stream sync).
 int radial_precompute(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const float* d_rij, bool deriv,
@@ -104,6 +121,13 @@ int radial_precompute(rascal_ctx* ctx, const rascal_system* sys, const int64_t* 
 int radial_exact_pairs(rascal_ctx* ctx, int64_t n, const float4* rij, float* out, float* dout) {
     const int n_max = ctx->n_max, L1 = ctx->l_max + 1;
     const double c = 1.0 / (2.0 * ctx->sigma * ctx->sigma);
+    if (ctx->basis == RASCAL_BASIS_DVR) {
+        if (n == 0) return RASCAL_OK;
+        k_exact_dvr<<<(unsigned)div_up(n * n_max, 128), 128, 0, ctx->stream>>>(n, rij, n_max, ctx->l_max, c, ctx->d_dvr,
+                                                                            out, dout);
+        RASCAL_LAUNCH_CHECK("k_exact_dvr");
+        return RASCAL_OK;
+    }
     const int64_t batch = std::min<int64_t>(n, 1 << 16);
     for (int64_t start = 0; start < n; start += batch) {
         const int64_t nb = std::min<int64_t>(batch, n - start);
