@@ -68,6 +68,9 @@ def parse_args(argv=None):
                          "(trained on the GPU before timing)")
     ap.add_argument("--basis", choices=["gto", "dvr"], default="gto",
                     help="radial basis: GTO (Eq. rad-int-gto-1, orthonormalised) or DVR (Eq. rad-int-dvr)")
+    ap.add_argument("--gpr", type=int, default=0,
+                    help="sparse points per species of a sparse GPR energy model (Eq. sparse-gp) on top of p; 0 = off")
+    ap.add_argument("--zeta", type=int, default=2, help="exponent of the GPR polynomial kernel")
     ap.add_argument("--mlp-steps", type=int, default=4000, help="Adam steps of the surrogate's training (setup)")
     ap.add_argument("--select", type=float, default=0.0,
                     help="fraction of the packed power-spectrum features to compute (seeded random selection; "
@@ -97,6 +100,43 @@ def load_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def load_tensor_peak():
+    """Dense BF16 tensor peak (TFLOP/s) measured as a burst, else the fallback figure."""
+    try:
+        with open(PEAKS_FILE) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def gpr_setup(args, calc, system, ds, coeffs, ps, sel, rg):
+    """A GPR model whose sparse points are the power spectra of seeded atoms of this rank's own workload (one
+    untimed soap pass), x_I ~ N(0, 1); returns the model and its config entry with the algorithmic flops of the
+    kernel GEMM (2 F sum_s N_s n_s over the centre species)."""
+    import numpy as np
+
+    from synth import gpr_sparse_draws
+
+    pairs = calc.neighbours(ds)
+    if sel is not None:
+        calc.soap_selected(ds, pairs, sel, coeffs=coeffs, ps=ps)
+    else:
+        calc.soap(ds, pairs, coeffs=coeffs, ps=ps)
+    idx, x = gpr_sparse_draws(system.species, calc.species, args.gpr, seed=31)
+    import torch
+
+    pm = ps[torch.as_tensor(idx, device=ps.device)].double().cpu().numpy()
+    model = rg.GprModel(calc, pm, system.species[idx], x, zeta=args.zeta)
+    lab = system.species
+    flops = 0.0
+    for s in calc.species:
+        flops += 2.0 * ps.shape[1] * np.count_nonzero(lab == s) * np.count_nonzero(system.species[idx] == s)
+    cfg = {"sparse_per_species": args.gpr, "n_sparse": int(idx.size), "zeta": args.zeta, "features": int(ps.shape[1]),
+           "precision": "tf32 operands, fp32 accumulate", "sparse_points": "p of seeded atoms of the workload"}
+    return model, {"config": cfg, "flops_energy": flops}
 
 
 class ClockSampler:
@@ -196,7 +236,11 @@ def cpu_worker(args):
 
         w = linear_weights(h.n_species, h.n_features("packed"), seed=4)
 
+    gpr_model = oracle_gpr_model(args, system, h) if args.gpr else None
+
     def run(centres):
+        if gpr_model is not None:
+            return oracle_gpr_step(args, system, h, gpr_model, centres)
         if w is not None:  # c, p, adjoint and per-pair gradients of the sampled centres' energy terms
             return osoap.energy_gradients(system, h, w, centres=centres)
         c = osoap.spherical_expansion(system, h, centres=centres)
@@ -216,11 +260,43 @@ def cpu_worker(args):
     print(json.dumps({"value": n / dt, "n": n, "seconds": dt}))
 
 
+def gpr_text(args):
+    return f" + sparse GPR energy ({args.gpr} sparse points per species, zeta {args.zeta})" if args.gpr else ""
+
+
+def oracle_gpr_model(args, system, h):
+    """The GPR model's sparse points as the oracle computes them (setup, untimed): the drawn atoms' FP64 p."""
+    from oracle import soap as osoap
+    from synth import gpr_sparse_draws
+
+    idx, x = gpr_sparse_draws(system.species, h.species, args.gpr, seed=31)
+    pm = osoap.power_spectrum(osoap.spherical_expansion(system, h, centres=idx), h, "packed").reshape(idx.size, -1)
+    return pm, h.species_index(system.species[idx]), x
+
+
+def oracle_gpr_step(args, system, h, model, centres):
+    """c, packed p, the GPR energies (and with --gradients dE/dp, forces and virial) of the sampled centres."""
+    import numpy as np
+
+    from oracle import gpr as ogpr
+    from oracle import soap as osoap
+
+    pm, ms, x = model
+    centres = np.asarray(centres)
+    cs = h.species_index(system.species[centres])
+    p = osoap.power_spectrum(osoap.spherical_expansion(system, h, centres=centres), h, "packed").reshape(centres.size, -1)
+    E = ogpr.energies(p, cs, pm, ms, x, args.zeta)
+    if args.gradients:
+        g = ogpr.grad_p(p, cs, pm, ms, x, args.zeta)
+        return E, osoap.energy_gradients(system, h, None, centres=centres, grad_p=g)
+    return E
+
+
 def cpu_baseline(args, cores=1):
     env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores),
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--config", args.config, "--layout", args.layout,
-           "--cpu-seconds", str(args.cpu_seconds), "--basis", args.basis] + (["--gradients"] if args.gradients else []) + \
+           "--cpu-seconds", str(args.cpu_seconds), "--basis", args.basis, "--gpr", str(args.gpr), "--zeta", str(args.zeta)] + (["--gradients"] if args.gradients else []) + \
           (["--expansion-only"] if args.expansion_only else [])
     res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     if res.returncode != 0:
@@ -229,7 +305,7 @@ def cpu_baseline(args, cores=1):
     return {"value": d["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{d['n']} seeded random centres of the {args.config} workload (neighbours + exact {'1F1' if args.basis == 'gto' else 'DVR'} coefficients"
                       f"{'' if args.expansion_only else ' + ' + args.layout + ' power spectrum'}"
-                      f"{' + forces and virial' if args.gradients else ''}, FP64 numpy), "
+                      f"{gpr_text(args)}{' + forces and virial' if args.gradients else ''}, FP64 numpy), "
                       f"{d['seconds']:.1f} s on one host thread"}
 
 
@@ -252,7 +328,11 @@ def run_reference(args):
 
         w = linear_weights(h.n_species, h.n_features("packed"), seed=4)
 
+    gpr_model = oracle_gpr_model(args, system, h) if args.gpr else None
+
     def run(idx):
+        if gpr_model is not None:
+            return oracle_gpr_step(args, system, h, gpr_model, idx)
         if w is not None:
             return osoap.energy_gradients(system, h, w, centres=idx)
         c = osoap.spherical_expansion(system, h, centres=idx)
@@ -281,7 +361,7 @@ def run_reference(args):
     value = per_step * args.steps / dt
     sample = (f"{per_step} seeded random centres per step of the {args.config} workload (neighbours + exact "
               f"{'1F1' if args.basis == 'gto' else 'DVR'} coefficients{'' if args.expansion_only else ' + ' + args.layout + ' power spectrum'}"
-              f"{' + forces and virial' if args.gradients else ''}, "
+              f"{gpr_text(args)}{' + forces and virial' if args.gradients else ''}, "
               f"FP64 numpy), one host thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -332,14 +412,19 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     radial_info = radial_setup(args, calc, system, dev, rg)
     weights = None
-    if args.gradients:
+    gpr_model, gpr_info = None, None
+    if args.gpr:
+        if args.layout != "packed" or args.expansion_only:
+            raise SystemExit("--gpr takes the packed power spectrum (or a selection of it)")
+        gpr_model, gpr_info = gpr_setup(args, calc, system, ds, coeffs, ps, sel, rg)
+    if args.gradients and gpr_model is None:
         from synth import linear_weights
 
         weights = torch.tensor(linear_weights(calc.n_species, calc.n_features("packed"), seed=4), dtype=torch.float32,
                                device=dev)
 
     def step(events=None):
-        # stage boundaries: neighbours | expansion (or fused soap) | power spectrum (separate form) | gradients
+        # stage boundaries: neighbours | expansion (or fused soap) | power spectrum (separate form) | GPR | gradients
         def mark(k):
             if events is not None:
                 events[k].record(stream)
@@ -359,10 +444,16 @@ def run_ours(args):
             calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps)
             mark(2)
         mark(3)
+        g = None
+        if gpr_model is not None:
+            _, _, g = gpr_model.predict(ds, ps, grad=args.gradients, atomic=False)
+        mark(4)
         if weights is not None:
             calc.linear_energy(ds, ps, weights)
             calc.gradients(ds, pairs, coeffs, weights=weights)
-        mark(4)
+        elif g is not None:
+            calc.gradients(ds, pairs, coeffs, grad_ps=g)
+        mark(5)
         return pairs
 
     for _ in range(max(args.warmup, 3)):
@@ -370,7 +461,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     n_pairs = pairs.n_pairs
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
@@ -387,8 +478,8 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = sampler.stop()
     launches = rg.launch_count() - launches0
-    stage = [[e[s].elapsed_time(e[s + 1]) for e in evs] for s in range(4)]
-    step_ms = [sum(stage[s][k] for s in range(4)) for k in range(args.steps)]
+    stage = [[e[s].elapsed_time(e[s + 1]) for e in evs] for s in range(5)]
+    step_ms = [sum(stage[s][k] for s in range(5)) for k in range(args.steps)]
     ms = sum(step_ms) / len(step_ms)
     ms = max_over_ranks(ms, dev)
     total_env = int(sum_over_ranks(N, dev))
@@ -410,11 +501,23 @@ def run_ours(args):
         cand["k_expansion (rascal_spherical_expansion)"] = (pair_in + c_bytes, mean[1])
         if not args.expansion_only:
             cand["power spectrum (rascal_power_spectrum)"] = (c_bytes + p_bytes, mean[2])
-    if weights is not None:
-        cand["k_gradients (rascal_linear_energy + rascal_gradients)"] = (None, mean[3])
+    if gpr_model is not None:
+        cand["rascal_gpr_predict (k_gpr_kernel" + (" + k_gpr_grad)" if args.gradients else ")")] = (None, mean[3])
+    if args.gradients:
+        cand["k_gradients (" + ("rascal_gradients on dE/dp)" if gpr_model is not None else
+                                "rascal_linear_energy + rascal_gradients)")] = (None, mean[4])
     kernel = max(cand, key=lambda k: cand[k][1])
     alg, t_ms = cand[kernel]
-    if kernel.startswith("k_gradients"):
+    if kernel.startswith("rascal_gpr_predict"):
+        flops = gpr_info["flops_energy"] * (2 if args.gradients else 1)
+        bf16, tf32_kind = load_tensor_peak()
+        tf32_peak = bf16 * 1.1 / 2.25
+        achieved = flops / (t_ms * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / tf32_peak, "traffic": None, "algorithmic_flops_per_launch": flops,
+                    "peak_source": f"TF32 = {tf32_kind} bf16 peak x 1.1/2.25 (nominal dense TF32/BF16 ratio); the "
+                                   "timed region is the whole call (species sort, GEMMs, finish)"}
+    elif kernel.startswith("k_gradients"):
         # per pair: s += chat dR Y and w += chat R grad Y over the centre's species block, 2 + 3 FMA per (n, lm);
         # per centre: the adjoint chat_l = k_l (W + W^T) C_l, Q x Q times Q x (2l+1)
         n_lm = (calc.l_max + 1) ** 2
@@ -440,7 +543,7 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e and world >= 1:
-        e2e = measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, weights=weights, sel=sel)
+        e2e = measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, weights=weights, sel=sel, gpr=gpr_model)
         e2e["ms"] = max_over_ranks(e2e["ms"], dev)
         e2e = {"value": total_env / (e2e["ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e["ms"]}
@@ -457,11 +560,13 @@ def run_ours(args):
                                                                           "fused": fused, "features": Fp,
                                                                           "selected": sel is not None},
                        "gradients": bool(args.gradients), "radial_basis": args.basis, **radial_info,
+                       **({"gpr": gpr_info["config"]} if gpr_info else {}),
                        "parallelism": f"dp{world} (independent batches per GPU)",
                        "l2": "256 MB buffer written before every timed step (L2 is 129 MB), outside the step events",
                        "stage_ms": {"neighbours": mean[0], ("expansion" if not fused else "soap"): mean[1],
                                     **({"power_spectrum": mean[2]} if args.separate else {}),
-                                    **({"gradients": mean[3]} if args.gradients else {})},
+                                    **({"gpr": mean[3]} if gpr_model is not None else {}),
+                                    **({"gradients": mean[4]} if args.gradients else {})},
                        "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -524,7 +629,7 @@ def coefficient_error(calc, ds, coeffs, rg, args):
     return {args.radial: err(mine, ref), "spline": err(spline, ref)}
 
 
-def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None, weights=None, sel=None):
+def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None, weights=None, sel=None, gpr=None):
     """Same step through the public API with host buffers: pinned H2D of the inputs, D2H of the power spectrum.
 
     Steps are pipelined the way a streaming user would run them: the power spectrum of step k leaves on a copy
@@ -544,12 +649,15 @@ def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None, wei
     }
     dev_t = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
     result = coeffs if args.expansion_only else ps  # the step's result read back by the host
+    if gpr is not None:  # the model's structure energies are the result; p stays on the device
+        result = torch.empty(system.n_structures, dtype=torch.float64, device=dev)
     ps_buf = [result, torch.empty_like(result)]
     out_host = [torch.empty(result.shape, dtype=result.dtype).pin_memory() for _ in range(2)]
     forces_host = torch.empty((system.n_atoms, 3), dtype=torch.float64).pin_memory()
     ds = rg.DeviceSystem(dev_t["positions"], dev_t["species"], dev_t["cells"], dev_t["pbc"], dev_t["struct_offsets"])
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = out_host[0].numel() * out_host[0].element_size() + (forces_host.numel() * 8 if weights is not None else 0)
+    d2h = out_host[0].numel() * out_host[0].element_size() + \
+        (forces_host.numel() * 8 if (weights is not None or (gpr is not None and args.gradients)) else 0)
     copy_stream = torch.cuda.Stream(dev)
     copied = [None, None]
 
@@ -569,9 +677,19 @@ def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None, wei
             calc.power_spectrum(coeffs, precision=args.ps, layout=args.layout, out=ps_buf[b])
         elif sel is not None:
             calc.soap_selected(ds, pairs, sel, coeffs=coeffs, ps=ps_buf[b])
+        elif gpr is not None:
+            if sel is not None:
+                calc.soap_selected(ds, pairs, sel, coeffs=coeffs, ps=ps)
+            else:
+                calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps)
         else:
             calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps_buf[b])
-        if weights is not None:
+        if gpr is not None:
+            e, _, g = gpr.predict(ds, ps, grad=args.gradients, atomic=False)
+            ps_buf[b].copy_(e)
+            if g is not None:
+                forces, _ = calc.gradients(ds, pairs, coeffs, grad_ps=g)
+        elif weights is not None:
             calc.linear_energy(ds, ps_buf[b], weights)
             forces, _ = calc.gradients(ds, pairs, coeffs, weights=weights)
         ready = torch.cuda.Event()

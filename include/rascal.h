@@ -212,6 +212,32 @@ int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d
                      const float* d_rij, const float* d_coeffs, const float* d_grad_ps, const float* d_weights,
                      double* d_forces, double* d_virial);
 
+/* Sparse GPR energy model (Eq. sparse-gp) with the polynomial kernel k(M_I, A_i) = (M^_I . p^_i)^zeta, one model
+ * per centre species: E_i = sum over the sparse points I of the centre's species of x_I k(M_I, A_i). With
+ * normalize = 1 both vectors are unit-normalised (p^ = p/|p|; a centre with p = 0 keeps p^ = 0), else used as given.
+ * The contractions run on the tensor cores with TF32 operands (the sparse points are rounded to the nearest TF32
+ * value at creation; the features are read as FP32 and truncated to TF32 by the tensor core) and FP32 accumulation:
+ * |E_i - exact| <= 2 zeta (2^-10 + 2^-11) sum_I |x_I| for unit vectors, plus FP32 summation.
+ *   h_sparse [n_sparse][n_features] float64, h_sparse_species [n_sparse] int32 labels (each one of the context's),
+ *   h_weights [n_sparse] float64 (x_I); all host memory, copied. n_features: length of the feature rows the
+ *   predictions take (the PACKED power spectrum or a selection of it). zeta in [1, 16].
+ * The model lives on the current device; it may be used with any context of the same species list. */
+typedef struct rascal_gpr rascal_gpr;
+int rascal_gpr_create(rascal_ctx* ctx, int64_t n_sparse, int64_t n_features, const double* h_sparse,
+                      const int* h_sparse_species, const double* h_weights, int zeta, int normalize, rascal_gpr** out);
+void rascal_gpr_destroy(rascal_gpr* model);
+
+/* Energies of the model for every atom of the system as a centre (Eq. sparse-gp), and optionally their gradients
+ * with respect to the features, summed over the sparse points first (Eq. gpr-force-order):
+ *   dE_i/dp_i = (G_i - zeta E_i p^_i) / |p_i|,  G_i = sum_I x_I zeta k_(zeta-1) M^_I   (|p_i| = 1 without normalisation)
+ * which rascal_gradients turns into forces and virial (its d_grad_ps argument).
+ *   d_features [n_atoms][n_features] float32, one row per centre in atom order (rows 16-byte aligned is fastest)
+ *   d_atomic [n_atoms] float32 E_i (may be NULL); d_energy [n_structures] float64 sum of E_i per structure, FP64
+ *   summation (may be NULL); d_grad [n_atoms][n_features] float32 (may be NULL: energies only)
+ * Asynchronous on the context stream; uses the context's scratch. */
+int rascal_gpr_predict(rascal_ctx* ctx, const rascal_gpr* model, const rascal_system* sys, const float* d_features,
+                       float* d_atomic, double* d_energy, float* d_grad);
+
 /* Exact FP64 o-GTO radial integrals I^o_nl(r) and their r-derivatives at n_points distances (Eq. rad-int-gto-1
  * with the 1F1 of Appendix A, then S^-1/2): d_r [n] float64, d_out and d_dout [n][n_max][l_max+1] float64
  * (d_dout may be NULL). Used to build the spline and the MLP training targets. */

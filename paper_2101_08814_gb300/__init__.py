@@ -307,3 +307,51 @@ class SoapCalculator:
         dout = torch.empty_like(out) if derivative else None
         _lib.check(_lib.lib().rascal_radial_exact_fp64(self._ctx, r.shape[0], _ptr(r), _ptr(out), _ptr(dout)))
         return (out, dout) if derivative else out
+
+
+class GprModel:
+    """Sparse GPR energy model with the polynomial kernel (Eq. sparse-gp), evaluated on the tensor cores.
+
+    sparse [n_sparse, n_features] (host array), sparse_species [n_sparse] labels, weights [n_sparse] (x_I)."""
+
+    def __init__(self, calc: SoapCalculator, sparse, sparse_species, weights, zeta=2, normalize=True):
+        import numpy as np
+
+        self.calc = calc
+        sp = np.ascontiguousarray(sparse, dtype=np.float64)
+        if sp.ndim != 2:
+            raise ValueError("sparse points must be a 2-D array [n_sparse, n_features]")
+        lab = np.ascontiguousarray(sparse_species, dtype=np.int32)
+        x = np.ascontiguousarray(weights, dtype=np.float64)
+        self.n_features = int(sp.shape[1])
+        self.zeta, self.normalize = int(zeta), bool(normalize)
+        self._h = C.c_void_p()
+        _lib.check(_lib.lib().rascal_gpr_create(calc._ctx, sp.shape[0], sp.shape[1], sp.ctypes.data_as(C.c_void_p),
+                                                lab.ctypes.data_as(C.c_void_p), x.ctypes.data_as(C.c_void_p),
+                                                self.zeta, int(self.normalize), C.byref(self._h)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _lib.lib().rascal_gpr_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def predict(self, system: DeviceSystem, features, grad=False, atomic=True):
+        """(per-structure energies float64, per-centre energies float32 or None, dE/dp float32 or None)."""
+        import torch
+
+        calc = self.calc
+        calc._bind_stream()
+        e = torch.empty(system.n_structures, dtype=torch.float64, device=calc.device)
+        ea = torch.empty(system.n_atoms, dtype=torch.float32, device=calc.device) if atomic else None
+        g = torch.empty((system.n_atoms, self.n_features), dtype=torch.float32, device=calc.device) if grad else None
+        f = features.reshape(system.n_atoms, -1)
+        if f.shape[1] != self.n_features or f.dtype != torch.float32 or not f.is_contiguous():
+            raise ValueError("features must be a contiguous float32 [n_atoms, n_features] tensor")
+        sys_c = system.c_struct()
+        _lib.check(_lib.lib().rascal_gpr_predict(calc._ctx, self._h, C.byref(sys_c), _ptr(f), _ptr(ea), _ptr(e), _ptr(g)))
+        return e, ea, g
+

@@ -112,6 +112,11 @@ _SIGNATURES = {
     "rascal_mlp_eval": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rascal_mlp_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "rascal_mlp_load": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "rascal_gpr_create": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                    C.c_int, C.POINTER(C.c_void_p)]),
+    "rascal_gpr_destroy": (None, [C.c_void_p]),
+    "rascal_gpr_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
 }
 
 

@@ -62,6 +62,22 @@ __device__ inline uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
     return d;                // base offset 0, no swizzle
 }
 
+// K-major operand in the 64-byte swizzled layout: 8-row atoms of 8 x 64 bytes (SBO between atoms), the 16-byte chunk
+// c of row r stored at chunk c ^ ((r >> 1) & 3), as a TMA load with 64-byte swizzling writes it. The start address
+// may be advanced by the K offset in bytes inside the atom; atoms start on 512-byte boundaries.
+__device__ inline uint64_t smem_desc_sw64(uint32_t saddr, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                     // leading byte offset: unused for swizzled K-major operands
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
+    d |= (uint64_t)4 << 61;                     // swizzling mode: 64 bytes
+    return d;
+}
+__device__ inline uint32_t sw64_off(int row, int chunk) {
+    return (uint32_t)((row >> 3) * 512 + (row & 7) * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
+}
+
 // instruction descriptor: D FP32, A/B format (1 = BF16 for kind::f16, 2 = TF32 for kind::tf32), K-major A and B
 __device__ inline uint32_t instr_desc(uint32_t ab_format, uint32_t M, uint32_t N) {
     return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
@@ -99,6 +115,19 @@ __device__ inline void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// TMA: 2-D tiled load of one box into shared memory (128-byte aligned destination; the innermost coordinate times
+// the element size a multiple of 16 bytes), completion counted in bytes on an mbarrier armed by expect_tx.
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ inline void tma_load_2d(void* sdst, const void* tmap, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(sdst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Bulk (non-tensor) asynchronous copy shared -> global by the issuing thread: both addresses 16-byte aligned,
 // size a multiple of 16 bytes. The writers of the source make their stores visible to the async proxy
 // (fence_proxy_async_smem) before the barrier that precedes the issue. Completion is tracked per thread in bulk
@@ -121,5 +150,20 @@ __device__ inline void cp_async4(void* sdst, const void* gsrc) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
 }
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// 16-byte (L2-only) and 4-byte copies that fill the destination with zeros beyond src_bytes (0 = all zeros, nothing
+// is read); grouped by commit_group, waited for by wait_group<N> (at most N of this thread's groups still pending)
+__device__ inline void cp_async16_zfill(void* sdst, const void* gsrc, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc), "r"(src_bytes)
+                 : "memory");
+}
+__device__ inline void cp_async4_zfill(void* sdst, const void* gsrc, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc), "r"(src_bytes)
+                 : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 }  // namespace rascal

@@ -17,4 +17,5 @@ from .structures import (  # noqa: F401
     mlp_initial_params,
     mlp_training_draws,
     small_cell_system,
+    gpr_sparse_draws,
 )

@@ -249,3 +249,15 @@ def linear_weights(n_species: int, n_features: int, seed: int = 4) -> np.ndarray
     """Gaussian N(0,1) weights of the additive linear energy model, one row per centre species."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal((n_species, n_features))
+
+
+def gpr_sparse_draws(species: np.ndarray, labels, n_per_species: int, seed: int = 31):
+    """Seeded choice of sparse points for a GPR model: `n_per_species` atoms of each label (all of them if fewer),
+    whose environments serve as the active set, and regression weights x_I ~ N(0, 1). Returns (atom indices, x)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    idx = []
+    for lab in labels:
+        cand = np.flatnonzero(species == lab)
+        idx.append(rng.choice(cand, size=min(n_per_species, cand.size), replace=False) if cand.size else cand)
+    idx = np.sort(np.concatenate(idx)).astype(np.int64)
+    return idx, rng.standard_normal(idx.size)
