@@ -118,8 +118,13 @@ __device__ inline void gpr_drain_tma(uint64_t* full, int stages, int64_t from, i
 }
 
 // ------------------------------------------------------------------------------------------ kernel GEMM
-// A (feature rows, gathered by atom) by cp.async into [8-row group][chunk][row][16 B]; B (sparse points) by TMA
-// into [chunk][512 rows][16 B] (boxes of 16 bytes x 64 rows).
+// Warp-specialised pipeline: warps 0-3 gather A (feature rows of the tile's centres) by cp.async into the 64-byte
+// swizzled layout and, once their own copies of a stage have landed, arrive on its `full` barrier; warp 4 loads B (the
+// species' sparse points) by TMA onto the same barrier and issues the MMAs, which release the stage through `empty`.
+// The row norms are accumulated by the A threads from their own chunks and reduced per tile.
+constexpr int kGprProducers = 128;  // A-copy threads (warps 0-3)
+constexpr int kGprLag = 3;          // k-blocks a producer keeps in flight before it waits for its oldest
+
 template <bool VEC16>
 __global__ void __launch_bounds__(kGprThreads, 1) k_gpr_kernel(const __grid_constant__ GprArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -127,8 +132,8 @@ __global__ void __launch_bounds__(kGprThreads, 1) k_gpr_kernel(const __grid_cons
     unsigned char* sB = sA + kGprStages * kGprATile;                 // [stages][32 KB]
     float* s_x = reinterpret_cast<float*>(sB + kGprStages * kGprB1);  // [512]
     float* s_inv = s_x + 512;                                        // [128]
-    float* s_E = s_inv + 128;                                        // [2][128]
-    int* s_atom = reinterpret_cast<int*>(s_E + 256);                 // [128]
+    float* s_E = s_inv + 128;                                        // [2][128]; [4][128] norm partials before
+    int* s_atom = reinterpret_cast<int*>(s_E + 512);                 // [128]
     int* s_off = s_atom + 128;                                       // [S + 1]
     int* s_per = s_off + kMaxSpecies + 1;                            // [S] passes per species
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_per + kMaxSpecies + 1);  // [stages] empty, [stages] full, done
@@ -145,7 +150,11 @@ __global__ void __launch_bounds__(kGprThreads, 1) k_gpr_kernel(const __grid_cons
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i <= 2 * kGprStages; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < kGprStages; ++i) {
+            mbar_init(&empty[i], 1);
+            mbar_init(&full[i], kGprProducers + 1);
+        }
+        mbar_init(done, 1);
         fence_mbar_init();
     }
     tc_fence_before();
@@ -153,9 +162,9 @@ __global__ void __launch_bounds__(kGprThreads, 1) k_gpr_kernel(const __grid_cons
     tc_fence_after();
     const uint32_t taddr = *s_tmem;
     const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
-    int64_t g = 0;          // k-blocks issued by this CTA so far (stage = g % stages, use = g / stages)
-    int64_t g_tma = 0;      // k-blocks whose B load thread 0 has issued
-    int64_t g_full = 0;     // k-blocks whose B load thread 0 has seen land
+    int64_t g = 0;          // k-blocks of this CTA so far (stage = g % stages, use = g / stages)
+    int64_t g_tma = 0;      // warp 4: k-blocks whose B load was issued
+    int64_t g_full = 0;     // warp 4: k-blocks whose stage it has seen full
     uint32_t done_phase = 0;
     bool ok = true;
 
@@ -165,120 +174,137 @@ __global__ void __launch_bounds__(kGprThreads, 1) k_gpr_kernel(const __grid_cons
         const int n_rows = min(128, s_off[s + 1] - row0);
         const int col0 = pass * 512;
         const int ncols = min(512, A.n_pad[s] - col0);
-        const int n0 = min(256, ncols), n1 = ncols - n0;
-        const int nq = (ncols + 63) / 64;                             // 64-row TMA boxes of B per chunk
-        const int brow = (int)(A.row_off[s] + col0);
+        const int nk = (int)(A.Fk / kGprKB);
         if (tid < 128) s_atom[tid] = tid < n_rows ? A.perm[row0 + tid] : -1;
         for (int c = tid; c < 512; c += blockDim.x) s_x[c] = c < ncols ? A.x[A.row_off[s] + col0 + c] : 0.0f;
         __syncthreads();
-        const int nk = (int)(A.Fk / kGprKB);
-        // per-thread copy plan for A, fixed for the tile: rows r0 and r0 + 64, 16 bytes at chunk c
-        const int r0 = tid >> 2, c = tid & 3;
-        const uint32_t d0 = sw64_off(r0, c);  // row r0 + 64 lands 4096 bytes further
-        const float* pa[2];
-        int64_t lim[2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int atom = s_atom[r0 + 64 * j];
-            pa[j] = atom >= 0 ? A.p + (int64_t)atom * A.F : A.p;
-            lim[j] = atom >= 0 ? A.F : 0;  // features of this row (0: zero fill)
-        }
 
-        auto load = [&](int kb, int stage) {
-            const int64_t k0 = (int64_t)kb * kGprKB;
-            unsigned char* a = sA + stage * kGprATile;
-            if (VEC16) {
+        if (warp < 4) {
+            // ---- A producers: rows r0 + 32 j (j < 4), 16-byte chunk c
+            const int r0 = tid >> 2, c = tid & 3;
+            const uint32_t d0 = sw64_off(r0, c);  // row r0 + 32 j lands 2048 j bytes further
+            const float* pa[4];
+            int64_t lim[4];
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const bool in = k0 + 4 * c < lim[j];
-                    cp_async16_zfill(a + d0 + 4096 * j, in ? pa[j] + k0 + 4 * c : A.p, in ? 16u : 0u);
+            for (int j = 0; j < 4; ++j) {
+                const int atom = s_atom[r0 + 32 * j];
+                pa[j] = atom >= 0 ? A.p + (int64_t)atom * A.F : A.p;
+                lim[j] = atom >= 0 ? A.F : 0;
+            }
+            float nrm[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            auto land = [&](int kb) {  // this thread's chunks of k-block kb are in shared memory: norms, arrive
+                const unsigned char* a = sA + (int)((g + kb) % kGprStages) * kGprATile + d0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 v = *reinterpret_cast<const float4*>(a + 2048 * j);
+                    nrm[j] = fmaf(v.x, v.x, nrm[j]);
+                    nrm[j] = fmaf(v.y, v.y, nrm[j]);
+                    nrm[j] = fmaf(v.z, v.z, nrm[j]);
+                    nrm[j] = fmaf(v.w, v.w, nrm[j]);
                 }
-            } else {
+                mbar_arrive(&full[(g + kb) % kGprStages]);
+            };
+            int landed = 0;
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int64_t gi = g + kb;
+                const int stage = (int)(gi % kGprStages);
+                if (gi >= kGprStages &&
+                    !mbar_wait_bounded(&empty[stage], (uint32_t)(((gi - kGprStages) / kGprStages) & 1))) {
+                    ok = false;
+                    break;
+                }
+                const int64_t k0 = (int64_t)kb * kGprKB;
+                unsigned char* a = sA + stage * kGprATile + d0;
+                if (VEC16) {
 #pragma unroll
-                for (int j = 0; j < 2; ++j)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const bool in = k0 + 4 * c + e < lim[j];
-                        cp_async4_zfill(a + d0 + 4096 * j + 4 * e, in ? pa[j] + k0 + 4 * c + e : A.p, in ? 4u : 0u);
-                    }
-            }
-            if (tid == 0) {
-                unsigned char* b = sB + stage * kGprB1;
-                mbar_expect_tx(&full[stage], (uint32_t)(nq * 4096));
-                for (int qq = 0; qq < nq; ++qq) tma_load_2d(b + qq * 4096, &A.tmM, (int)k0, brow + 64 * qq, &full[stage]);
-                ++g_tma;
-            }
-        };
-
-        for (int i = 0; i < kGprStages - 1; ++i) {
-            if (i < nk) load(i, (int)((g + i) % kGprStages));
-            cp_async_commit();
-        }
-        float nrm = 0.0f;
-        const uint32_t id0 = instr_desc(2u, 128u, (uint32_t)n0);
-        const uint32_t id1 = instr_desc(2u, 128u, (uint32_t)max(n1, 16));
-        int kb = 0;
-        for (; kb < nk; ++kb) {
-            const int64_t gi = g + kb;
-            const int stage = (int)(gi % kGprStages);
-            cp_async_wait_group<kGprStages - 2>();
-            fence_proxy_async_smem();
-            if (!__syncthreads_and(ok)) {  // a bounded wait ran out in some thread: every thread stops here
-                ok = false;
-                break;
-            }
-            if (tid == 0) {
-                if (mbar_wait_bounded(&full[stage], (uint32_t)((gi / kGprStages) & 1))) {
-                    ++g_full;
-                    tc_fence_after();
-                    const uint32_t a0 = a_base + stage * kGprATile, b0 = b_base + stage * kGprB1;
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint64_t da = smem_desc_sw64(a0 + kk * 32, 512);
-                        mma_tf32_ss(taddr, da, smem_desc_sw64(b0 + kk * 32, 512), id0, (kb | kk) != 0);
-                        if (n1 > 0) mma_tf32_ss(taddr + 256, da, smem_desc_sw64(b0 + 16384 + kk * 32, 512), id1, (kb | kk) != 0);
+                    for (int j = 0; j < 4; ++j) {
+                        const bool in = k0 + 4 * c < lim[j];
+                        cp_async16_zfill(a + 2048 * j, in ? pa[j] + k0 + 4 * c : A.p, in ? 16u : 0u);
                     }
                 } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const bool in = k0 + 4 * c + e < lim[j];
+                            cp_async4_zfill(a + 2048 * j + 4 * e, in ? pa[j] + k0 + 4 * c + e : A.p, in ? 4u : 0u);
+                        }
+                }
+                cp_async_commit();
+                if (kb >= kGprLag) {
+                    cp_async_wait_group<kGprLag>();
+                    fence_proxy_async_smem();
+                    land(landed++);
+                }
+            }
+            cp_async_wait_group<0>();
+            fence_proxy_async_smem();
+            while (ok && landed < nk) land(landed++);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s_E[c * 128 + r0 + 32 * j] = nrm[j];  // partials [chunk][row]
+        } else if (warp == 4) {
+          if (lane == 0) {
+            // ---- B loads and MMAs
+            const int n0 = min(256, ncols), n1 = ncols - n0;
+            const int nq = (ncols + 63) / 64;
+            const int brow = (int)(A.row_off[s] + col0);
+            const uint32_t id0 = instr_desc(2u, 128u, (uint32_t)n0);
+            const uint32_t id1 = instr_desc(2u, 128u, (uint32_t)max(n1, 16));
+            auto load_b = [&](int kb) {
+                const int stage = (int)((g + kb) % kGprStages);
+                unsigned char* b = sB + stage * kGprB1;
+                mbar_expect_tx(&full[stage], (uint32_t)(nq * 4096));
+                for (int qq = 0; qq < nq; ++qq)
+                    tma_load_2d(b + qq * 4096, &A.tmM, kb * kGprKB, brow + 64 * qq, &full[stage]);
+                ++g_tma;
+            };
+            for (int i = 0; i < kGprStages - 1 && i < nk; ++i) load_b(i);
+            for (int kb = 0; kb < nk; ++kb) {
+                const int64_t gi = g + kb;
+                const int stage = (int)(gi % kGprStages);
+                if (!mbar_wait_bounded(&full[stage], (uint32_t)((gi / kGprStages) & 1))) {
                     ok = false;
+                    break;
+                }
+                ++g_full;
+                tc_fence_after();
+                const uint32_t a0 = a_base + stage * kGprATile, b0 = b_base + stage * kGprB1;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint64_t da = smem_desc_sw64(a0 + kk * 32, 512);
+                    mma_tf32_ss(taddr, da, smem_desc_sw64(b0 + kk * 32, 512), id0, (kb | kk) != 0);
+                    if (n1 > 0) mma_tf32_ss(taddr + 256, da, smem_desc_sw64(b0 + 16384 + kk * 32, 512), id1, (kb | kk) != 0);
                 }
                 mma_commit(&empty[stage]);
-            }
-            if (tid < 128) {  // row norms from the staged A tile (this thread's row, 16 features)
-                const unsigned char* a = sA + stage * kGprATile;
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {  // the row's 64 bytes, in any chunk order
-                    const float4 v = *reinterpret_cast<const float4*>(a + (tid >> 3) * 512 + (tid & 7) * 64 + cc * 16);
-                    nrm = fmaf(v.x, v.x, nrm);
-                    nrm = fmaf(v.y, v.y, nrm);
-                    nrm = fmaf(v.z, v.z, nrm);
-                    nrm = fmaf(v.w, v.w, nrm);
+                const int nxt = kb + kGprStages - 1;
+                if (nxt < nk) {
+                    if (gi >= 1 && !mbar_wait_bounded(&empty[(gi - 1) % kGprStages], (uint32_t)(((gi - 1) / kGprStages) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    load_b(nxt);
                 }
             }
-            // refill the stage the previous k-block used, once its MMAs are done
-            const int nxt = kb + kGprStages - 1;
-            if (nxt < nk && ok) {
-                const int64_t prev = gi - 1;
-                if (prev >= 0 && !mbar_wait_bounded(&empty[prev % kGprStages], (uint32_t)((prev / kGprStages) & 1)))
-                    ok = false;
-                if (ok) load(nxt, (int)((g + nxt) % kGprStages));
-            }
-            cp_async_commit();
+            mma_commit(done);
+          }
+          __syncwarp();  // the other lanes of the MMA warp wait here, not in a spin beside lane 0
         }
         g += nk;
-        if (tid == 0) mma_commit(done);
         const bool fin = mbar_wait_bounded(done, done_phase);
         done_phase ^= 1u;
-        if (tid < 128) {
-            const float iv = (A.normalize && nrm > 0.0f) ? 1.0f / sqrtf(nrm) : 1.0f;
-            s_inv[tid] = iv;
-            if (pass == 0 && s_atom[tid] >= 0) A.inv[s_atom[tid]] = iv;
-        }
         ok = __syncthreads_and(ok && fin) != 0;
         if (!ok) {
-            if (tid == 0) gpr_drain_tma(full, kGprStages, g_full, g_tma);
+            if (warp == 4 && lane == 0) gpr_drain_tma(full, kGprStages, g_full, g_tma);
             gpr_fail(A, done, done_phase ^ 1u);
             break;
         }
+        if (tid < 128) {
+            const float nn = s_E[tid] + s_E[128 + tid] + s_E[256 + tid] + s_E[384 + tid];
+            const float iv = (A.normalize && nn > 0.0f) ? 1.0f / sqrtf(nn) : 1.0f;
+            s_inv[tid] = iv;
+            if (pass == 0 && s_atom[tid] >= 0) A.inv[s_atom[tid]] = iv;
+        }
+        __syncthreads();
         tc_fence_after();
         // epilogue: warp -> lane quadrant (rows) and column half
         const int q = warp & 3, h = warp >> 2, row = 32 * q + lane;
@@ -305,6 +331,7 @@ __global__ void __launch_bounds__(kGprThreads, 1) k_gpr_kernel(const __grid_cons
                     *reinterpret_cast<float4*>(wrow + cc + u) = make_float4(w[u], w[u + 1], w[u + 2], w[u + 3]);
             }
         }
+        __syncthreads();  // the norm partials in s_E are read; the energies may reuse it
         s_E[h * 128 + row] = e;
         tc_fence_before();
         __syncthreads();
@@ -409,6 +436,7 @@ __global__ void __launch_bounds__(kGprThreads, 2) k_gpr_grad(const __grid_consta
                 mma_commit(done);
                 if (!ok) gpr_drain_tma(full, kGprStages2, g + kb, g + issued);
             }
+            if (warp == 0) __syncwarp();
             g += nk;
             const bool fin = mbar_wait_bounded(done, done_phase);
             done_phase ^= 1u;
@@ -427,7 +455,20 @@ __global__ void __launch_bounds__(kGprThreads, 2) k_gpr_grad(const __grid_consta
         const float iv = atom >= 0 && nk > 0 ? A.inv[atom] : 0.0f;
         const float cc = atom >= 0 && nk > 0 ? A.c2[atom] : 0.0f;
         const int c_end = min(ncols, 128 * h + 128);
+        // the feature values of the next 16 columns are requested before this group's are used (latency overlap)
+        const float* pbase = atom >= 0 ? A.p + (int64_t)atom * A.F : A.p;
+        auto fetch = [&](int c, float4 (&pv)[4]) {
+            const int64_t f = f0 + c;
+            if (atom >= 0 && A.vec16 && f + 16 <= A.F) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) pv[u] = __ldcs(reinterpret_cast<const float4*>(pbase + f) + u);
+            }
+        };
+        float4 pn[4];
+        if (128 * h < c_end) fetch(128 * h, pn);
         for (int c = 128 * h; c < c_end; c += 16) {
+            float4 pc[4] = {pn[0], pn[1], pn[2], pn[3]};
+            if (c + 16 < c_end) fetch(c + 16, pn);
             float v[16];
             if (nk > 0) {
                 tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
@@ -441,14 +482,13 @@ __global__ void __launch_bounds__(kGprThreads, 2) k_gpr_grad(const __grid_consta
             float* grow = A.grad + (int64_t)atom * A.F + f;
             if (A.vec16 && f + 16 <= A.F) {
 #pragma unroll
-                for (int u = 0; u < 16; u += 4) {
-                    const float4 pv = *reinterpret_cast<const float4*>(prow + u);
+                for (int u = 0; u < 4; ++u) {
                     float4 o;
-                    o.x = fmaf(iv, v[u], -cc * pv.x);
-                    o.y = fmaf(iv, v[u + 1], -cc * pv.y);
-                    o.z = fmaf(iv, v[u + 2], -cc * pv.z);
-                    o.w = fmaf(iv, v[u + 3], -cc * pv.w);
-                    *reinterpret_cast<float4*>(grow + u) = o;
+                    o.x = fmaf(iv, v[4 * u], -cc * pc[u].x);
+                    o.y = fmaf(iv, v[4 * u + 1], -cc * pc[u].y);
+                    o.z = fmaf(iv, v[4 * u + 2], -cc * pc[u].z);
+                    o.w = fmaf(iv, v[4 * u + 3], -cc * pc[u].w);
+                    __stcs(reinterpret_cast<float4*>(grow) + u, o);
                 }
             } else {
 #pragma unroll
@@ -560,7 +600,7 @@ __global__ void k_gpr_finish(int N, int S, int passes_max, const int* __restrict
 }
 
 static size_t gpr_smem1() {
-    return (size_t)kGprStages * (kGprATile + kGprB1) + sizeof(float) * (512 + 128 + 256) + sizeof(int) * 128 +
+    return (size_t)kGprStages * (kGprATile + kGprB1) + sizeof(float) * (512 + 128 + 512) + sizeof(int) * 128 +
            sizeof(int) * 2 * (kMaxSpecies + 1) + sizeof(uint64_t) * (2 * kGprStages + 1) + 16;
 }
 static size_t gpr_smem2() {

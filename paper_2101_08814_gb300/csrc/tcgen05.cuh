@@ -31,6 +31,9 @@ __device__ inline void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
+__device__ inline void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ inline void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
