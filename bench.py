@@ -71,6 +71,8 @@ def parse_args(argv=None):
     ap.add_argument("--gpr", type=int, default=0,
                     help="sparse points per species of a sparse GPR energy model (Eq. sparse-gp) on top of p; 0 = off")
     ap.add_argument("--zeta", type=int, default=2, help="exponent of the GPR polynomial kernel")
+    ap.add_argument("--lambda-soap", type=int, default=-1, dest="lambda_soap",
+                    help="rank of nu = 2 equivariants computed from c instead of the power spectrum; -1 = off")
     ap.add_argument("--mlp-steps", type=int, default=4000, help="Adam steps of the surrogate's training (setup)")
     ap.add_argument("--select", type=float, default=0.0,
                     help="fraction of the packed power-spectrum features to compute (seeded random selection; "
@@ -239,6 +241,10 @@ def cpu_worker(args):
     gpr_model = oracle_gpr_model(args, system, h) if args.gpr else None
 
     def run(centres):
+        if args.lambda_soap >= 0:
+            from oracle import lambda_soap as ols
+
+            return ols.equivariants(osoap.spherical_expansion(system, h, centres=centres), h, args.lambda_soap)
         if gpr_model is not None:
             return oracle_gpr_step(args, system, h, gpr_model, centres)
         if w is not None:  # c, p, adjoint and per-pair gradients of the sampled centres' energy terms
@@ -261,6 +267,8 @@ def cpu_worker(args):
 
 
 def gpr_text(args):
+    if args.lambda_soap >= 0:
+        return f" -> rank-{args.lambda_soap} nu = 2 equivariants instead of p"
     return f" + sparse GPR energy ({args.gpr} sparse points per species, zeta {args.zeta})" if args.gpr else ""
 
 
@@ -296,7 +304,8 @@ def cpu_baseline(args, cores=1):
     env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores),
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--config", args.config, "--layout", args.layout,
-           "--cpu-seconds", str(args.cpu_seconds), "--basis", args.basis, "--gpr", str(args.gpr), "--zeta", str(args.zeta)] + (["--gradients"] if args.gradients else []) + \
+           "--cpu-seconds", str(args.cpu_seconds), "--basis", args.basis, "--gpr", str(args.gpr), "--zeta", str(args.zeta),
+           "--lambda-soap", str(args.lambda_soap)] + (["--gradients"] if args.gradients else []) + \
           (["--expansion-only"] if args.expansion_only else [])
     res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     if res.returncode != 0:
@@ -331,6 +340,10 @@ def run_reference(args):
     gpr_model = oracle_gpr_model(args, system, h) if args.gpr else None
 
     def run(idx):
+        if args.lambda_soap >= 0:
+            from oracle import lambda_soap as ols
+
+            return ols.equivariants(osoap.spherical_expansion(system, h, centres=idx), h, args.lambda_soap)
         if gpr_model is not None:
             return oracle_gpr_step(args, system, h, gpr_model, idx)
         if w is not None:
@@ -408,7 +421,15 @@ def run_ours(args):
         sel = torch.tensor(np.sort(np.random.default_rng(11).choice(Fpk, n_sel, replace=False)).astype(np.int32),
                            device=dev)
         Fp = n_sel
-    ps = torch.empty((N, Fp), dtype=torch.float32, device=dev)
+    lsoap = None
+    if args.lambda_soap >= 0:
+        if args.gpr or args.gradients or sel is not None:
+            raise SystemExit("--lambda-soap replaces the power spectrum; it does not combine with --gpr/--gradients/--select")
+        n_pairs_l, feat_l = calc.lambda_soap_size(args.lambda_soap)
+        lsoap = torch.empty((N, n_pairs_l, 2 * args.lambda_soap + 1, calc.n_species * calc.n_max,
+                             calc.n_species * calc.n_max), dtype=torch.float32, device=dev)
+        Fp = feat_l
+    ps = torch.empty((N, Fp if lsoap is None else 1), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     radial_info = radial_setup(args, calc, system, dev, rg)
     weights = None
@@ -432,7 +453,11 @@ def run_ours(args):
         mark(0)
         pairs = calc.neighbours(ds)
         mark(1)
-        if args.separate or args.expansion_only:
+        if lsoap is not None:
+            calc.spherical_expansion(ds, pairs, out=coeffs)
+            mark(2)
+            calc.lambda_soap(coeffs, args.lambda_soap, out=lsoap)
+        elif args.separate or args.expansion_only:
             calc.spherical_expansion(ds, pairs, out=coeffs)
             mark(2)
             if not args.expansion_only:
@@ -491,7 +516,7 @@ def run_ours(args):
     pair_in = 24 * n_pairs + 8 * (N + 1)                      # r_ji float4 + j + species(j); CSR offsets
     c_bytes = 4 * Qc * N
     p_bytes = 4 * Fp * N
-    fused = not (args.separate or args.expansion_only)
+    fused = not (args.separate or args.expansion_only or lsoap is not None)
     peak, peak_kind = load_peaks()
     peak_src = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s"
     cand = {"rascal_neighbours": (None, mean[0])}
@@ -499,7 +524,9 @@ def run_ours(args):
         cand["k_expansion<fused power spectrum> (rascal_soap)"] = (pair_in + c_bytes + p_bytes, mean[1])
     else:
         cand["k_expansion (rascal_spherical_expansion)"] = (pair_in + c_bytes, mean[1])
-        if not args.expansion_only:
+        if lsoap is not None:
+            cand["k_lambda_soap (rascal_lambda_soap)"] = (c_bytes + 4 * lsoap.numel(), mean[2])
+        elif not args.expansion_only:
             cand["power spectrum (rascal_power_spectrum)"] = (c_bytes + p_bytes, mean[2])
     if gpr_model is not None:
         cand["rascal_gpr_predict (k_gpr_kernel" + (" + k_gpr_grad)" if args.gradients else ")")] = (None, mean[3])
@@ -542,6 +569,9 @@ def run_ours(args):
         del radial_info["check_error"]
 
     e2e = None
+    if lsoap is not None:
+        # the equivariants are GBs per step: reading them back every step would time the PCIe/C2C link alone
+        args.no_e2e = True
     if not args.no_e2e and world >= 1:
         e2e = measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, weights=weights, sel=sel, gpr=gpr_model)
         e2e["ms"] = max_over_ranks(e2e["ms"], dev)
@@ -556,7 +586,9 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}", "global_batch": total_env,
                        "env_per_gpu": N, "pairs_per_gpu": n_pairs,
-                       "power_spectrum": None if args.expansion_only else {"layout": args.layout, "precision": args.ps,
+                       **({"lambda_soap": {"lambda": args.lambda_soap, "features": Fp}} if lsoap is not None else {}),
+                       "power_spectrum": None if (args.expansion_only or lsoap is not None) else {"layout": args.layout,
+                                                                                                   "precision": args.ps,
                                                                           "fused": fused, "features": Fp,
                                                                           "selected": sel is not None},
                        "gradients": bool(args.gradients), "radial_basis": args.basis, **radial_info,
@@ -565,6 +597,7 @@ def run_ours(args):
                        "l2": "256 MB buffer written before every timed step (L2 is 129 MB), outside the step events",
                        "stage_ms": {"neighbours": mean[0], ("expansion" if not fused else "soap"): mean[1],
                                     **({"power_spectrum": mean[2]} if args.separate else {}),
+                                    **({"lambda_soap": mean[2]} if lsoap is not None else {}),
                                     **({"gpr": mean[3]} if gpr_model is not None else {}),
                                     **({"gradients": mean[4]} if args.gradients else {})},
                        "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps},

@@ -238,6 +238,19 @@ void rascal_gpr_destroy(rascal_gpr* model);
 int rascal_gpr_predict(rascal_ctx* ctx, const rascal_gpr* model, const rascal_system* sys, const float* d_features,
                        float* d_atomic, double* d_energy, float* d_grad);
 
+/* nu = 2 equivariants (lambda-SOAP) of rank lambda from the density coefficients (Sec. 'Experimental features': the
+ * correlation of Eq. body-order-x at nu = 2 coupled to rank lambda):
+ *   T^{lambda mu}_{(q1 l1)(q2 l2)} = sum_{m1 m2} <l1 m1; l2 m2 | lambda mu>_real c_{q1 l1 m1} c_{q2 l2 m2}
+ * with the Clebsch-Gordan coefficients carried into the real harmonic basis of the coefficients. Only proper tensors
+ * (l1 + l2 + lambda even) and pairs l1 <= l2 are formed (T(l2, l1) is the transpose of T(l1, l2)), ordered by l1 then
+ * l2. lambda = 0 gives (-1)^l times the power spectrum. FP32 arithmetic.
+ *   d_coeffs [n_centres][n_species][n_max][(l_max+1)^2] float32 (the rascal_spherical_expansion layout)
+ *   d_out [n_centres][n_pairs][2 lambda + 1][Q][Q] float32, Q = n_species n_max, 16-byte aligned
+ * 0 <= lambda <= 2 l_max, else RASCAL_E_ARG. The coupling tables are built on the host on the first call per lambda
+ * (a synchronous upload) and kept in the context. */
+int rascal_lambda_soap_size(const rascal_ctx* ctx, int lambda, int* n_pairs, int64_t* features_per_centre);
+int rascal_lambda_soap(rascal_ctx* ctx, int64_t n_centres, const float* d_coeffs, int lambda, float* d_out);
+
 /* Exact FP64 o-GTO radial integrals I^o_nl(r) and their r-derivatives at n_points distances (Eq. rad-int-gto-1
  * with the 1F1 of Appendix A, then S^-1/2): d_r [n] float64, d_out and d_dout [n][n_max][l_max+1] float64
  * (d_dout may be NULL). Used to build the spline and the MLP training targets. */

@@ -217,6 +217,25 @@ class SoapCalculator:
                                                _ptr(forces), _ptr(virial)))
         return forces, virial
 
+    def lambda_soap_size(self, lam: int):
+        """(number of (l1, l2) pairs, features per centre) of the rank-lam equivariants."""
+        n_pairs, feat = C.c_int(), C.c_int64()
+        _lib.check(_lib.lib().rascal_lambda_soap_size(self._ctx, int(lam), C.byref(n_pairs), C.byref(feat)))
+        return n_pairs.value, feat.value
+
+    def lambda_soap(self, coeffs, lam: int, out=None):
+        """nu = 2 equivariants of rank lam: [N, n_pairs, 2 lam + 1, Q, Q] float32 from c [N, S, n_max, n_lm]."""
+        import torch
+
+        self._bind_stream()
+        n_pairs, _ = self.lambda_soap_size(lam)
+        N = coeffs.shape[0]
+        Q = self.n_species * self.n_max
+        o = out if out is not None else torch.empty((N, n_pairs, 2 * lam + 1, Q, Q), dtype=torch.float32,
+                                                    device=self.device)
+        _lib.check(_lib.lib().rascal_lambda_soap(self._ctx, N, _ptr(coeffs), int(lam), _ptr(o)))
+        return o
+
     # ---------------------------------------------------------------------------------------- radial source
     def set_radial(self, mode: str):
         """'spline' (table), 'exact' (per-pair 1F1 in FP64) or 'mlp' (the trained network)."""

@@ -64,6 +64,8 @@ struct Arena {
 //   block start lp(l); Lp = sum_l mp(l)
 //   a task is (l, n-tile of 4, m-tile of 4) of one species: T_s tasks per species, W_s warps per species,
 //   S_c species accumulated concurrently, rounds = ceil(n_species / S_c)
+struct LsoapTable;  // lambda-SOAP coupling tables (lambda_soap.cu)
+
 struct ExpPlan {
     int n_pad, F_pad, Lp;
     int Ly;           // Y row pitch in the expansion kernel: Lp rounded up so that Ly / 4 is odd (conflict-free rows)
@@ -128,6 +130,9 @@ struct rascal_ctx {
     void* mlp_w2t;       // BF16 operand tiles for the tensor-core inference
     void* mlp_w3t;
     int mlp_hidden, mlp_step;
+
+    // real Clebsch-Gordan tables of the nu = 2 equivariants, built on first use per lambda (lambda_soap.cu)
+    rascal::LsoapTable* lsoap[2 * rascal::kMaxLMax + 1];
 };
 
 namespace rascal {
@@ -185,5 +190,6 @@ int power_spectrum_setup(rascal_ctx* ctx);
 // BF16 / TF32x3 power spectrum of given coefficients [n][Q][n_lm] by the fused kernel's tensor-core Gram
 int power_spectrum_tc(rascal_ctx* ctx, int64_t n_centres, const float* d_coeffs, int precision, int layout, float* d_ps);
 int gradients_setup(rascal_ctx* ctx);
+void lsoap_free(rascal_ctx* ctx);
 
 }  // namespace rascal

@@ -454,6 +454,7 @@ extern "C" void rascal_destroy(rascal_ctx* ctx) {
     cudaFree(ctx->scratch.ptr);
     cudaFree(ctx->scratch_w.ptr);
     cudaFree(ctx->d_dvr);
+    lsoap_free(ctx);
     cudaFree(ctx->scratch_sel.ptr);
     cudaFree(ctx->scratch2.ptr);
     delete ctx;
