@@ -6,13 +6,14 @@
 // for l1 + l2 + lambda even. Only those proper tensors are formed (the improper-rotation average of Eq. body-order-x
 // removes the others), and only l1 <= l2: T(l2, l1) is the transpose of T(l1, l2).
 //
-// Host: Racah's closed form for the CG coefficients in FP64, the unitary U per l, the real tables per (l1, l2),
-// cached per lambda in the context. Device: one CTA per centre; per pair the two coefficient blocks are staged in
+// Host: Racah's closed form for the CG coefficients in FP64, the unitary U per l, the real tables per (l1, l2), kept
+// as their (at most two) non-zero m1 terms per (mu, m2), cached per lambda in the context. Device: one CTA per centre; per pair the two coefficient blocks are staged in
 // shared memory, then per chunk of mu the half-contractions X[q1][m2] = sum_m1 R c_{q1 l1 m1} and the output tiles
 // T[q1][q2] = sum_m2 X[q1][m2] c_{q2 l2 m2}, written with streaming 16-byte stores. Bound: HBM (the output).
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -22,8 +23,9 @@ namespace rascal {
 struct LsoapTable {
     int lambda = -1;
     int n_pairs = 0;
-    int4* d_hdr = nullptr;  // per pair: l1, l2, offset of its table in d_R, 0
-    float* d_R = nullptr;   // per pair [2 lambda + 1][2 l1 + 1][2 l2 + 1]
+    int4* d_hdr = nullptr;   // per pair: l1, l2, offset of its entries in d_R, 0
+    float4* d_R = nullptr;   // per pair [2 lambda + 1][2 l2 + 1]: the (at most two) non-zero m1 terms of R[mu][.][m2]
+                             // as {value0, value1, m1_0 * Q, m1_1 * Q} (offsets as integer bits; value 0 pads)
 };
 
 static double fact(int n) {
@@ -111,7 +113,7 @@ constexpr int kLsoapXFloats = 6144;  // shared-memory budget of one X buffer (24
 
 __global__ void __launch_bounds__(256) k_lambda_soap(int64_t n, const float* __restrict__ c, int Q, int n_lm, int kmax,
                                                      int lam, int mchunk, int n_pairs, const int4* __restrict__ hdr,
-                                                     const float* __restrict__ R, float* __restrict__ out) {
+                                                     const float4* __restrict__ R, float* __restrict__ out) {
     extern __shared__ __align__(16) float sm[];
     const int i = blockIdx.x;
     if (i >= n) return;
@@ -136,8 +138,8 @@ __global__ void __launch_bounds__(256) k_lambda_soap(int64_t n, const float* __r
     __syncthreads();
     for (int p = 0; p < n_pairs; ++p) {
         const int4 h = hdr[p];
-        const int l1 = h.x, l2 = h.y, d1 = 2 * l1 + 1, d2 = 2 * l2 + 1;
-        const float* Rp = R + h.z;
+        const int l1 = h.x, l2 = h.y, d2 = 2 * l2 + 1;
+        const float4* Rp = R + h.z;
         const float* A = cT + l1 * l1 * Q;  // A[m1][q]
         const float* B = cT + l2 * l2 * Q;  // B[m2][q]
         const int b_c = threadIdx.x % d2, b_r = threadIdx.x / d2, b_s = blockDim.x / d2;
@@ -146,13 +148,20 @@ __global__ void __launch_bounds__(256) k_lambda_soap(int64_t n, const float* __r
             const int mc = min(mchunk, M - mu0);
             float* sX = buf ? sX1 : sX0;
             if (b_on) {
-                for (int u = 0; u < mc; ++u) {
-                    const float* Rm = Rp + (size_t)(mu0 + u) * d1 * d2 + b_c;
-                    float* xu = sX + (size_t)u * Q * d2 + b_c;
-                    for (int q1 = b_r; q1 < Q; q1 += b_s) {
-                        float x = 0.0f;
-                        for (int m1 = 0; m1 < d1; ++m1) x = fmaf(__ldg(Rm + m1 * d2), A[m1 * Q + q1], x);
-                        xu[q1 * d2] = x;
+                // rows rr = u Q + q1 of X over the whole chunk, so that all mc * Q rows share the threads evenly
+                int u = 0, q1 = b_r;
+                while (q1 >= Q) {
+                    q1 -= Q;
+                    ++u;
+                }
+                for (int rr = b_r; rr < mc * Q; rr += b_s) {
+                    const float4 e = __ldg(Rp + (size_t)(mu0 + u) * d2 + b_c);  // the two non-zero m1 of this (mu, m2)
+                    const float x = fmaf(e.x, A[__float_as_int(e.z) + q1], e.y * A[__float_as_int(e.w) + q1]);
+                    sX[(size_t)rr * d2 + b_c] = x;
+                    q1 += b_s;
+                    while (q1 >= Q) {
+                        q1 -= Q;
+                        ++u;
                     }
                 }
             }
@@ -160,10 +169,12 @@ __global__ void __launch_bounds__(256) k_lambda_soap(int64_t n, const float* __r
             float* o = out + (((int64_t)i * n_pairs + p) * M + mu0) * QQ;
             if (vec) {
                 if (t_on) {
-                    for (int u = 0; u < mc; ++u) {
-                        for (int rp = t_r; rp < nq1; rp += r_step) {
-                            const int q1 = 2 * rp, q2 = 4 * t_q2;
-                            const float* x0 = sX + ((size_t)u * Q + q1) * d2;
+                    // row pairs over the whole chunk: row 2 rp of [mc Q][..] is (u, q1) = (2 rp / Q, 2 rp % Q), and both
+                    // X and the output of consecutive mu are contiguous, so no division is needed
+                    for (int rp = t_r; rp < mc * nq1; rp += r_step) {
+                        {
+                            const int q2 = 4 * t_q2;
+                            const float* x0 = sX + (size_t)(2 * rp) * d2;
                             float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
                             for (int m2 = 0; m2 < d2; ++m2) {
                                 const float4 bv = *reinterpret_cast<const float4*>(B + m2 * Q + q2);
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(256) k_lambda_soap(int64_t n, const float* __r
                                 b.z = fmaf(xb, bv.z, b.z);
                                 b.w = fmaf(xb, bv.w, b.w);
                             }
-                            float* ou = o + u * QQ + (int64_t)q1 * Q + q2;
+                            float* ou = o + (int64_t)(2 * rp) * Q + q2;
                             __stcs(reinterpret_cast<float4*>(ou), a);
                             __stcs(reinterpret_cast<float4*>(ou + Q), b);
                         }
@@ -195,29 +206,48 @@ __global__ void __launch_bounds__(256) k_lambda_soap(int64_t n, const float* __r
     }
 }
 
-int lsoap_table(rascal_ctx* ctx, int lam, int* n_pairs, const int4** hdr, const float** R) {
+int lsoap_table(rascal_ctx* ctx, int lam, int* n_pairs, const int4** hdr, const float4** R) {
     if (lam < 0 || lam > 2 * ctx->l_max) return set_error(RASCAL_E_ARG, "lambda must be in [0, 2 l_max] = [0, %d]", 2 * ctx->l_max);
     LsoapTable*& tab = ctx->lsoap[lam];
     if (!tab) {
         std::vector<int2> P;
         lsoap_pairs(ctx->l_max, lam, P);
         std::vector<int4> h(P.size());
-        std::vector<float> all, one;
+        std::vector<float4> all;
+        std::vector<float> one;
+        const int Q = ctx->Q;
         for (size_t k = 0; k < P.size(); ++k) {
-            if (!real_table(P[k].x, P[k].y, lam, one))
-                return set_error(RASCAL_E_UNSUPPORTED, "coupling (%d, %d) -> %d is not real", P[k].x, P[k].y, lam);
-            h[k] = make_int4(P[k].x, P[k].y, (int)all.size(), 0);
-            all.insert(all.end(), one.begin(), one.end());
+            const int l1 = P[k].x, l2 = P[k].y, d1 = 2 * l1 + 1, d2 = 2 * l2 + 1;
+            if (!real_table(l1, l2, lam, one))
+                return set_error(RASCAL_E_UNSUPPORTED, "coupling (%d, %d) -> %d is not real", l1, l2, lam);
+            h[k] = make_int4(l1, l2, (int)all.size(), 0);
+            for (int u = 0; u < 2 * lam + 1; ++u)
+                for (int m2 = 0; m2 < d2; ++m2) {
+                    float v[2] = {0.0f, 0.0f};
+                    int o[2] = {0, 0}, nz = 0;
+                    for (int m1 = 0; m1 < d1; ++m1) {
+                        const float r = one[((size_t)u * d1 + m1) * d2 + m2];
+                        if (std::fabs(r) < 1e-7f) continue;  // exact zeros up to the rounding of the FP64 sums
+                        if (nz == 2)
+                            return set_error(RASCAL_E_UNSUPPORTED, "coupling (%d, %d) -> %d has more than two terms",
+                                             l1, l2, lam);
+                        v[nz] = r;
+                        o[nz++] = m1 * Q;
+                    }
+                    float f[2];
+                    std::memcpy(f, o, sizeof(f));  // offsets travel as integer bits
+                    all.push_back(make_float4(v[0], v[1], f[0], f[1]));
+                }
         }
         LsoapTable* t = new LsoapTable();
         t->lambda = lam;
         t->n_pairs = (int)P.size();
         cudaError_t e = cudaMalloc(&t->d_hdr, sizeof(int4) * std::max<size_t>(1, h.size()));
-        if (e == cudaSuccess) e = cudaMalloc(&t->d_R, sizeof(float) * std::max<size_t>(1, all.size()));
+        if (e == cudaSuccess) e = cudaMalloc(&t->d_R, sizeof(float4) * std::max<size_t>(1, all.size()));
         if (e == cudaSuccess && !h.empty())
             e = cudaMemcpy(t->d_hdr, h.data(), sizeof(int4) * h.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && !all.empty())
-            e = cudaMemcpy(t->d_R, all.data(), sizeof(float) * all.size(), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(t->d_R, all.data(), sizeof(float4) * all.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             cudaFree(t->d_hdr);
             cudaFree(t->d_R);
@@ -264,7 +294,7 @@ extern "C" int rascal_lambda_soap(rascal_ctx* ctx, int64_t n_centres, const floa
     if (n_centres < 0) return set_error(RASCAL_E_ARG, "negative n_centres");
     int np;
     const int4* hdr;
-    const float* R;
+    const float4* R;
     int st = lsoap_table(ctx, lambda, &np, &hdr, &R);
     if (st) return st;
     if (n_centres == 0 || np == 0) return RASCAL_OK;
