@@ -703,18 +703,21 @@ def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None, wei
             dev_t[key].copy_(host[key], non_blocking=True)
         pairs = calc.neighbours(ds)
         forces = None
-        if args.expansion_only:
+        if gpr is not None:  # p stays on the device; the result buffers hold the structure energies
+            if args.separate:
+                calc.spherical_expansion(ds, pairs, out=coeffs)
+                calc.power_spectrum(coeffs, precision=args.ps, layout=args.layout, out=ps)
+            elif sel is not None:
+                calc.soap_selected(ds, pairs, sel, coeffs=coeffs, ps=ps)
+            else:
+                calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps)
+        elif args.expansion_only:
             calc.spherical_expansion(ds, pairs, out=ps_buf[b])
         elif args.separate:
             calc.spherical_expansion(ds, pairs, out=coeffs)
             calc.power_spectrum(coeffs, precision=args.ps, layout=args.layout, out=ps_buf[b])
         elif sel is not None:
             calc.soap_selected(ds, pairs, sel, coeffs=coeffs, ps=ps_buf[b])
-        elif gpr is not None:
-            if sel is not None:
-                calc.soap_selected(ds, pairs, sel, coeffs=coeffs, ps=ps)
-            else:
-                calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps)
         else:
             calc.soap(ds, pairs, layout=args.layout, precision=args.ps, coeffs=coeffs, ps=ps_buf[b])
         if gpr is not None:

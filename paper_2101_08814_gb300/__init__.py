@@ -18,6 +18,19 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
 
 
+def _need(t, numel: int, what: str):
+    """A caller-provided buffer must be a contiguous float32 tensor with room for `numel` values: the library writes
+    through raw pointers and cannot check sizes itself."""
+    import torch
+
+    if t is None:
+        return t
+    if t.dtype != torch.float32 or not t.is_contiguous() or t.device.type != "cuda" or t.numel() < numel:
+        raise ValueError(f"{what}: need a contiguous float32 CUDA tensor of at least {numel} values, got "
+                         f"{tuple(t.shape)} {t.dtype} on {t.device}")
+    return t
+
+
 def launch_count() -> int:
     """Kernels the library has launched in this process (all contexts)."""
     return int(_lib.lib().rascal_launch_count())
@@ -150,8 +163,8 @@ class SoapCalculator:
 
         self._bind_stream()
         N = system.n_atoms
-        c = out if out is not None else torch.empty((N, self.n_species, self.n_max, (self.l_max + 1) ** 2),
-                                                    dtype=torch.float32, device=self.device)
+        c = _need(out, N * self.coeffs_per_centre, "out") if out is not None else \
+            torch.empty((N, self.n_species, self.n_max, (self.l_max + 1) ** 2), dtype=torch.float32, device=self.device)
         sys_c = system.c_struct()
         _lib.check(_lib.lib().rascal_spherical_expansion(self._ctx, C.byref(sys_c), _ptr(pairs.offsets),
                                                          _ptr(pairs.nbr_j), _ptr(pairs.rij), _ptr(c)))
@@ -162,7 +175,9 @@ class SoapCalculator:
 
         self._bind_stream()
         n = int(coeffs.shape[0])
-        p = out if out is not None else torch.empty((n, self.n_features(layout)), dtype=torch.float32, device=self.device)
+        _need(coeffs, n * self.coeffs_per_centre, "coeffs")
+        p = _need(out, n * self.n_features(layout), "out") if out is not None else \
+            torch.empty((n, self.n_features(layout)), dtype=torch.float32, device=self.device)
         _lib.check(_lib.lib().rascal_power_spectrum(self._ctx, n, _ptr(coeffs), PRECISION[precision], LAYOUT[layout],
                                                     _ptr(p)))
         return p
@@ -173,9 +188,10 @@ class SoapCalculator:
 
         self._bind_stream()
         N = system.n_atoms
-        c = coeffs if coeffs is not None else torch.empty((N, self.n_species, self.n_max, (self.l_max + 1) ** 2),
-                                                          dtype=torch.float32, device=self.device)
-        p = ps if ps is not None else torch.empty((N, self.n_features(layout)), dtype=torch.float32, device=self.device)
+        c = _need(coeffs, N * self.coeffs_per_centre, "coeffs") if coeffs is not None else \
+            torch.empty((N, self.n_species, self.n_max, (self.l_max + 1) ** 2), dtype=torch.float32, device=self.device)
+        p = _need(ps, N * self.n_features(layout), "ps") if ps is not None else \
+            torch.empty((N, self.n_features(layout)), dtype=torch.float32, device=self.device)
         sys_c = system.c_struct()
         _lib.check(_lib.lib().rascal_soap(self._ctx, C.byref(sys_c), _ptr(pairs.offsets), _ptr(pairs.nbr_j),
                                           _ptr(pairs.rij), PRECISION[precision], LAYOUT[layout], _ptr(c), _ptr(p)))
@@ -188,9 +204,10 @@ class SoapCalculator:
         self._bind_stream()
         N = system.n_atoms
         sel = torch.as_tensor(sel, dtype=torch.int32, device=self.device).contiguous()
-        c = coeffs if coeffs is not None else torch.empty((N, self.n_species, self.n_max, (self.l_max + 1) ** 2),
-                                                          dtype=torch.float32, device=self.device)
-        p = ps if ps is not None else torch.empty((N, sel.numel()), dtype=torch.float32, device=self.device)
+        c = _need(coeffs, N * self.coeffs_per_centre, "coeffs") if coeffs is not None else \
+            torch.empty((N, self.n_species, self.n_max, (self.l_max + 1) ** 2), dtype=torch.float32, device=self.device)
+        p = _need(ps, N * sel.numel(), "ps") if ps is not None else \
+            torch.empty((N, sel.numel()), dtype=torch.float32, device=self.device)
         sys_c = system.c_struct()
         _lib.check(_lib.lib().rascal_soap_selected(self._ctx, C.byref(sys_c), _ptr(pairs.offsets), _ptr(pairs.nbr_j),
                                                    _ptr(pairs.rij), int(sel.numel()), _ptr(sel), _ptr(c), _ptr(p)))
@@ -200,6 +217,8 @@ class SoapCalculator:
         import torch
 
         self._bind_stream()
+        _need(ps_packed, system.n_atoms * self.n_features("packed"), "ps_packed")
+        _need(weights, self.n_species * self.n_features("packed"), "weights")
         e = torch.empty(system.n_structures, dtype=torch.float64, device=self.device)
         sys_c = system.c_struct()
         _lib.check(_lib.lib().rascal_linear_energy(self._ctx, C.byref(sys_c), _ptr(ps_packed), _ptr(weights), _ptr(e)))
@@ -209,6 +228,10 @@ class SoapCalculator:
         import torch
 
         self._bind_stream()
+        N = system.n_atoms
+        _need(coeffs, N * self.coeffs_per_centre, "coeffs")
+        _need(grad_ps, N * self.n_features("packed"), "grad_ps")
+        _need(weights, self.n_species * self.n_features("packed"), "weights")
         forces = torch.empty((system.n_atoms, 3), dtype=torch.float64, device=self.device)
         virial = torch.empty((system.n_structures, 3, 3), dtype=torch.float64, device=self.device)
         sys_c = system.c_struct()
@@ -231,8 +254,9 @@ class SoapCalculator:
         n_pairs, _ = self.lambda_soap_size(lam)
         N = coeffs.shape[0]
         Q = self.n_species * self.n_max
-        o = out if out is not None else torch.empty((N, n_pairs, 2 * lam + 1, Q, Q), dtype=torch.float32,
-                                                    device=self.device)
+        _need(coeffs, N * self.coeffs_per_centre, "coeffs")
+        o = _need(out, N * n_pairs * (2 * lam + 1) * Q * Q, "out") if out is not None else \
+            torch.empty((N, n_pairs, 2 * lam + 1, Q, Q), dtype=torch.float32, device=self.device)
         _lib.check(_lib.lib().rascal_lambda_soap(self._ctx, N, _ptr(coeffs), int(lam), _ptr(o)))
         return o
 
