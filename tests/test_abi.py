@@ -60,3 +60,17 @@ def test_error_path_without_device(library):
     st = _lib.lib().rascal_create(None, None, ctypes.byref(out))
     assert st == _lib.RASCAL_E_ARG
     assert b"NULL" in _lib.lib().rascal_last_error()
+
+
+def test_binding_rejects_undersized_or_foreign_buffers():
+    """Caller-provided buffers are checked before any call: the library writes through raw pointers."""
+    import pytest
+    import torch
+
+    from paper_2101_08814_gb300 import _need
+
+    assert _need(None, 10, "x") is None
+    with pytest.raises(ValueError):
+        _need(torch.zeros(10), 10, "x")  # not on a CUDA device
+    with pytest.raises(ValueError):
+        _need(torch.zeros(10, dtype=torch.float64), 5, "x")
