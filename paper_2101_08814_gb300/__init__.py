@@ -391,7 +391,7 @@ class GprModel:
         e = torch.empty(system.n_structures, dtype=torch.float64, device=calc.device)
         ea = torch.empty(system.n_atoms, dtype=torch.float32, device=calc.device) if atomic else None
         g = torch.empty((system.n_atoms, self.n_features), dtype=torch.float32, device=calc.device) if grad else None
-        f = features.reshape(system.n_atoms, -1)
+        f = features.reshape(system.n_atoms, self.n_features)
         if f.shape[1] != self.n_features or f.dtype != torch.float32 or not f.is_contiguous():
             raise ValueError("features must be a contiguous float32 [n_atoms, n_features] tensor")
         sys_c = system.c_struct()

@@ -254,3 +254,52 @@ def test_model_errors(rg):
         rg.GprModel(calc, np.ones((2, 5)), [1, 99], [1.0, 1.0])
     with pytest.raises(rg.RascalError):
         rg.GprModel(calc, np.ones((2, 5)), [1, 1], [1.0, 1.0], zeta=0)
+
+
+def _isolated_system():
+    pos = np.array([[1.0, 1.0, 1.0], [2.0, 2.0, 2.0], [9.0, 9.0, 9.0]])
+    cells = np.stack([np.eye(3) * 30.0] * 3)
+    return System(pos, np.array([14, 14, 14], np.int32), cells, np.array([[1, 1, 1], [0, 0, 0], [1, 1, 1]], np.int32),
+                  np.array([0, 1, 1, 3], np.int32), dict(r_cut=5.0, sigma=0.5, n_max=2, l_max=1, smooth_width=0.5,
+                                                           species=[14]))
+
+
+def test_isolated_atoms_empty_structure_and_model_without_points(rg):
+    """p = 0 rows (isolated atoms: E = 0, the unnormalised gradient), an empty structure, no atoms at all, and a
+    model with no sparse points (E = 0, dE/dp = 0)."""
+    import torch
+
+    s = _isolated_system()
+    calc = rg.SoapCalculator(**s.hypers)
+    ds = rg.DeviceSystem.from_numpy(s)
+    c, p = calc.soap(ds, calc.neighbours(ds))
+    F = p.shape[1]
+    rng = np.random.default_rng(2)
+    M = np.abs(rng.normal(size=(5, F)))
+    x = rng.standard_normal(5)
+    for zeta in (1, 2):
+        model = rg.GprModel(calc, M, [14] * 5, x, zeta=zeta)
+        e, ea, g = model.predict(ds, p, grad=True)
+        calc.sync()
+        p64 = p.double().cpu().numpy()
+        assert np.all(p64 == 0.0)
+        assert np.all(e.cpu().numpy() == 0.0) and np.all(ea.cpu().numpy() == 0.0)
+        g_ref = ogpr.grad_p(p64, np.zeros(3, int), M, np.zeros(5, int), x, zeta)
+        # zeta = 1: dE/dp = sum_I x_I M^_I, each term carrying the TF32 rounding of x_I and M^_I (2^-10 + 2^-11);
+        # zeta >= 2: exactly 0
+        Mh = M / np.linalg.norm(M, axis=1, keepdims=True)
+        bound = 2.0 ** -9 * (np.abs(x) @ np.abs(Mh)) + 1e-7
+        err = np.abs(g.cpu().numpy() - g_ref)
+        print(f"p = 0 rows, zeta {zeta}: max |dg| / bound = {np.max(err / bound[None, :]):.3f}")
+        assert np.all(err <= bound[None, :])
+    empty = rg.GprModel(calc, np.zeros((0, F)), [], [], zeta=2)
+    e, ea, g = empty.predict(ds, p, grad=True)
+    calc.sync()
+    assert np.all(e.cpu().numpy() == 0.0) and np.all(g.cpu().numpy() == 0.0)
+    # no atoms at all
+    s0 = System(np.zeros((0, 3)), np.zeros(0, np.int32), np.eye(3)[None] * 10.0, np.ones((1, 3), np.int32),
+                np.array([0, 0], np.int32), s.hypers)
+    ds0 = rg.DeviceSystem.from_numpy(s0)
+    e0, _, g0 = rg.GprModel(calc, M, [14] * 5, x).predict(ds0, torch.zeros((0, F), device=calc.device), grad=True)
+    calc.sync()
+    assert e0.shape == (1,) and float(e0.cpu()[0]) == 0.0 and g0.shape == (0, F)

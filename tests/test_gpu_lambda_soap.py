@@ -86,3 +86,19 @@ def test_lambda_range(rg):
         calc.lambda_soap(c, -1)
     n_pairs, _ = calc.lambda_soap_size(2 * calc.l_max)
     assert n_pairs == 1
+
+
+def test_no_centres_and_isolated_atoms(rg):
+    import torch
+
+    from synth import System
+
+    pos = np.array([[1.0, 1.0, 1.0], [9.0, 9.0, 9.0]])
+    s = System(pos, np.array([14, 14], np.int32), np.eye(3)[None] * 30.0, np.ones((1, 3), np.int32),
+               np.array([0, 2], np.int32), dict(r_cut=5.0, sigma=0.5, n_max=2, l_max=2, smooth_width=0.5, species=[14]))
+    calc, c = _gpu_c(rg, s)
+    T = calc.lambda_soap(c, 2)
+    assert np.all(T.cpu().numpy() == 0.0)
+    T0 = calc.lambda_soap(torch.zeros((0, 1, 2, 9), device=calc.device), 1)
+    calc.sync()
+    assert T0.shape[0] == 0
