@@ -15,7 +15,14 @@ from ._lib import LAYOUT, PRECISION, RADIAL, RascalError  # noqa: F401
 
 
 def _ptr(t):
-    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+    """Device address of a tensor. An empty view (e.g. the pair arrays of a system without pairs) reports 0 from
+    data_ptr(); its storage address is passed instead, so that the library's NULL checks only reject missing buffers."""
+    if t is None:
+        return C.c_void_p(0)
+    p = t.data_ptr()
+    if p == 0 and t.numel() == 0:
+        p = t.untyped_storage().data_ptr()
+    return C.c_void_p(p)
 
 
 def _need(t, numel: int, what: str):

@@ -74,3 +74,14 @@ def test_binding_rejects_undersized_or_foreign_buffers():
         _need(torch.zeros(10), 10, "x")  # not on a CUDA device
     with pytest.raises(ValueError):
         _need(torch.zeros(10, dtype=torch.float64), 5, "x")
+
+
+def test_empty_views_keep_their_storage_address():
+    """A system without pairs hands the library empty slices of allocated pair arrays: their address is passed."""
+    import torch
+
+    from paper_2101_08814_gb300 import _ptr
+
+    base = torch.empty(8)
+    assert _ptr(base[:0]).value == base.data_ptr()
+    assert _ptr(None).value is None
