@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kGprThreads, 2) k_gpr_grad(const __grid_consta
             const int64_t f = f0 + c;
             if (atom >= 0 && A.vec16 && f + 16 <= A.F) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) pv[u] = __ldcs(reinterpret_cast<const float4*>(pbase + f) + u);
+                for (int u = 0; u < 4; ++u) pv[u] = __ldg(reinterpret_cast<const float4*>(pbase + f) + u);
             }
         };
         float4 pn[4];
