@@ -31,7 +31,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + written) per environment of the fused pair kernel with the FP32 power spectrum
 # (k_expansion<kGramSimt>, PACKED layout) on the batch workload's recipe, from one ncu capture of a 96-cell case:
-# (8.853 MB + 850.582 MB) / 13 434 environments (profiles/k_expansion_fused_fp32_batch96.md). Scaled to a full
+# (8.853 MB + 850.582 MB) / 13 434 environments (dram__bytes_read.sum + dram__bytes_write.sum). Scaled to a full
 # launch by the environments it processes; valid only while that kernel is unchanged.
 FUSED_FP32_TRAFFIC_PER_ENV = (8.853e6 + 850.582e6) / 13434
 

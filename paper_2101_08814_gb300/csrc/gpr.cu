@@ -624,7 +624,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // with 64-byte swizzling (the operand layout of smem_desc_sw64); reads past the last row fill zeros
 static int tmap_2d(CUtensorMap* m, const float* base, uint64_t cols, uint64_t rows, uint64_t pitch) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    if (!fn) return set_error(RASCAL_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if (!fn) return set_error(RASCAL_E_CUDA, "cuTensorMapEncodeTiled is not available from the CUDA driver library");
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {pitch * sizeof(float)};
     cuuint32_t box[2] = {16, 64};
