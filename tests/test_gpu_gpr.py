@@ -228,23 +228,22 @@ def test_forces_of_the_gpr_energy_match_the_oracle(rg):
     E_ref = ogpr.energies(p_ref, cs, pm, ms, x, zeta)
     g_ref = ogpr.grad_p(p_ref, cs, pm, ms, x, zeta)
     F_ref, V_ref = osoap.energy_gradients(s, h, None, grad_p=g_ref)
-    F_g, V_g = osoap.energy_gradients(s, h, None, grad_p=g.cpu().numpy())
     F, V = F.cpu().numpy(), V.cpu().numpy()
     scale = zeta * np.sum(np.abs(x))
-    print("E err", np.max(np.abs(ea.cpu().numpy() - E_ref)) / scale, "F err", np.max(np.abs(F - F_ref)) / np.max(np.abs(F_ref)),
-          "F vs oracle on GPU dE/dp", np.max(np.abs(F - F_g)) / np.max(np.abs(F_g)))
-    assert np.max(np.abs(ea.cpu().numpy() - E_ref)) <= 2.0 ** -9.4 * scale
-    # the gradient kernel on the GPU's own dE/dp: the FP32 bar of the linear model
-    assert np.max(np.abs(F - F_g)) <= 1e-4 * np.max(np.abs(F_g))
-    assert np.max(np.abs(V - V_g)) <= 1e-4 * np.max(np.abs(V_g))
-    # dE/dp within its bound, then the forces it gives against FP64 (reported; the TF32 error of dE/dp enters
-    # linearly and is bounded above)
-    pgpu = p.cpu().numpy()
-    r_emul, r_exact = _grad_checks(g.cpu().numpy(), pgpu, cs, tf32_nearest(pm / np.linalg.norm(pm, axis=1,
-                                   keepdims=True)).astype(np.float64), ms, x, zeta, pm)
-    print(f"whole path dE/dp error/allowed: emulated {r_emul:.3f}, exact {r_exact:.3f}")
-    assert r_emul <= 1.0 and r_exact <= 1.0
-    assert np.max(np.abs(F - F_ref)) <= 2e-2 * np.max(np.abs(F_ref))
+    e_err = np.max(np.abs(ea.cpu().numpy() - E_ref)) / scale
+    f_err = np.max(np.abs(F - F_ref)) / np.max(np.abs(F_ref))
+    print("E err", e_err, "F err", f_err)
+    assert e_err <= 2.0 ** -9.4
+    # the gradient kernel on the oracle's own dE/dp (rounded to FP32): the FP32 bar of the linear model
+    g32 = g_ref.astype(np.float32)
+    F_k, V_k = calc.gradients(ds, pairs, c, grad_ps=torch.tensor(g32, device=calc.device))
+    calc.sync()
+    F_kr, V_kr = osoap.energy_gradients(s, h, None, grad_p=g32.astype(np.float64))
+    assert np.max(np.abs(F_k.cpu().numpy() - F_kr)) <= 1e-4 * np.max(np.abs(F_kr))
+    assert np.max(np.abs(V_k.cpu().numpy() - V_kr)) <= 1e-4 * np.max(np.abs(V_kr))
+    # end to end against FP64: dE/dp carries the TF32 rounding bounded in the tests above (forces are linear in it)
+    assert f_err <= 5e-3
+    assert np.max(np.abs(V - V_ref)) <= 5e-3 * np.max(np.abs(V_ref))
 
 
 def test_model_errors(rg):
@@ -303,3 +302,42 @@ def test_isolated_atoms_empty_structure_and_model_without_points(rg):
     e0, _, g0 = rg.GprModel(calc, M, [14] * 5, x).predict(ds0, torch.zeros((0, F), device=calc.device), grad=True)
     calc.sync()
     assert e0.shape == (1,) and float(e0.cpu()[0]) == 0.0 and g0.shape == (0, F)
+
+
+def test_batch_full_size_sampled(rg):
+    """The bench's configuration: batch workload, fused FP32 p, 512 sparse points per species (from the oracle's p of
+    the drawn atoms), zeta 2; energies and dE/dp of sampled centres against FP64 on the oracle's p."""
+    from synth import config_batch
+
+    s = config_batch()
+    h = osoap.Hypers(**s.hypers)
+    calc = rg.SoapCalculator(**s.hypers)
+    ds = rg.DeviceSystem.from_numpy(s)
+    pairs = calc.neighbours(ds)
+    c, p = calc.soap(ds, pairs)
+    idx, x = gpr_sparse_draws(s.species, h.species, 512, seed=31)
+    pm = osoap.power_spectrum(osoap.spherical_expansion(s, h, centres=idx), h, "packed").reshape(idx.size, -1)
+    model = rg.GprModel(calc, pm, s.species[idx], x, zeta=2)
+    e, ea, g = model.predict(ds, p, grad=True)
+    calc.sync()
+    rng = np.random.default_rng(3)
+    centres = np.concatenate([[0, s.n_atoms - 1], rng.choice(s.n_atoms, 14, replace=False)])
+    p_ref = osoap.power_spectrum(osoap.spherical_expansion(s, h, centres=centres), h, "packed").reshape(centres.size, -1)
+    a = h.species_index(s.species)
+    ms = h.species_index(s.species[idx])
+    E_ref = ogpr.energies(p_ref, a[centres], pm, ms, x, 2)
+    g_ref = ogpr.grad_p(p_ref, a[centres], pm, ms, x, 2)
+    scale = 2 * np.sum(np.abs(x[ms == a[0]]))  # |x| of one species' points bounds that species' energies
+    e_err = np.max(np.abs(ea.cpu().numpy()[centres] - E_ref))
+    g_gpu = g[_on_device(centres, g)].cpu().numpy()
+    g_err = np.max(np.abs(g_gpu - g_ref)) / np.max(np.abs(g_ref))
+    print(f"batch: |dE| {e_err:.3e} (bound unit {scale:.3e}), dE/dp max-relative {g_err:.3e}")
+    assert e_err <= 2.0 ** -9 * 2 * np.sum(np.abs(x))
+    assert g_err <= 1e-2
+    assert np.isfinite(e.cpu().numpy()).all()
+
+
+def _on_device(idx, like):
+    import torch
+
+    return torch.as_tensor(idx, device=like.device)

@@ -102,3 +102,22 @@ def test_no_centres_and_isolated_atoms(rg):
     T0 = calc.lambda_soap(torch.zeros((0, 1, 2, 9), device=calc.device), 1)
     calc.sync()
     assert T0.shape[0] == 0
+
+
+def test_batch_full_size_sampled(rg):
+    """The bench's configuration: batch workload, c from the expansion kernel, rank 1 (17.8 GB of output)."""
+    import torch
+
+    from synth import config_batch
+
+    s = config_batch()
+    h = osoap.Hypers(**s.hypers)
+    calc, c = _gpu_c(rg, s)
+    T = calc.lambda_soap(c, 1)
+    rng = np.random.default_rng(4)
+    centres = np.concatenate([[0, s.n_atoms - 1], rng.choice(s.n_atoms, 10, replace=False)])
+    Ts = T[torch.as_tensor(centres, device=T.device)].cpu().numpy()
+    calc.sync()
+    del T
+    T_ref = ols.equivariants(osoap.spherical_expansion(s, h, centres=centres), h, 1)
+    assert block_rel_err(Ts, T_ref, 2) <= 1e-5
