@@ -59,7 +59,8 @@ def parse_args(argv=None):
                     help="rascal_spherical_expansion + rascal_power_spectrum instead of the fused rascal_soap")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=24.0,
+                    help="host seconds of oracle work in the CPU baseline, split over its three modes")
     ap.add_argument("--structures", type=int, default=512, help="cells in the batch workload (profiling cases)")
     ap.add_argument("--gradients", action="store_true",
                     help="add the linear energy model and its forces and virial (rascal_linear_energy + rascal_gradients)")
@@ -220,50 +221,133 @@ def sum_over_ranks(x, device):
 
 
 # ---------------------------------------------------------------------------------------------------- CPU oracle
-def cpu_worker(args):
-    """Times the FP64 oracle on a bounded, seeded sample of centres of the workload (single host thread)."""
-    import numpy as np
-
+def oracle_step_fn(args, system, h, radial_fn=None):
+    """One oracle pass over a list of centres for the workload the flags describe (FP64 numpy); radial_fn, when
+    given, replaces the exact radial integrals (the FP64 spline mode)."""
     from oracle import soap as osoap
-
-    system = make_system(args.config, 0)
-    system.hypers = dict(system.hypers, basis=args.basis)
-    h = osoap.Hypers(**system.hypers)
-    rng = np.random.default_rng(123)
-    order = rng.permutation(system.n_atoms)
 
     w = None
     if args.gradients:
         from synth import linear_weights
 
         w = linear_weights(h.n_species, h.n_features("packed"), seed=4)
-
     gpr_model = oracle_gpr_model(args, system, h) if args.gpr else None
 
     def run(centres):
         if args.lambda_soap >= 0:
             from oracle import lambda_soap as ols
 
-            return ols.equivariants(osoap.spherical_expansion(system, h, centres=centres), h, args.lambda_soap)
+            return ols.equivariants(osoap.spherical_expansion(system, h, centres=centres, radial_fn=radial_fn), h,
+                                    args.lambda_soap)
         if gpr_model is not None:
-            return oracle_gpr_step(args, system, h, gpr_model, centres)
+            return oracle_gpr_step(args, system, h, gpr_model, centres, radial_fn)
         if w is not None:  # c, p, adjoint and per-pair gradients of the sampled centres' energy terms
-            return osoap.energy_gradients(system, h, w, centres=centres)
-        c = osoap.spherical_expansion(system, h, centres=centres)
+            return osoap.energy_gradients(system, h, w, centres=centres, radial_fn=radial_fn)
+        c = osoap.spherical_expansion(system, h, centres=centres, radial_fn=radial_fn)
         return c if args.expansion_only else osoap.power_spectrum(c, h, args.layout)
 
-    run(order[:2])  # first call builds the oracle's per-(a, b) 1F1 switch points
-    start, n = 2, 16
-    while True:  # grow the sample until one run takes about cpu_seconds
-        n = int(min(n, system.n_atoms - start))
+    return run
+
+
+_POOL = {}
+
+
+def _pool_init(argv, system, spline):
+    # each process runs one host thread (the environment carries OMP_NUM_THREADS=1 and friends)
+    from oracle import soap as osoap
+
+    args = parse_args(argv)
+    h = osoap.Hypers(**system.hypers)
+    fn = (lambda r, d=False: spline(r, d)) if spline is not None else None
+    _POOL["run"] = oracle_step_fn(args, system, h, fn)
+    _POOL["run"]([0, 1])  # builds the per-process 1F1 switch points before the timed region
+
+
+def _pool_task(centres):
+    _POOL["run"](centres)
+    return len(centres)
+
+
+def _time_serial(run, order, start, seconds):
+    """Grows a sample of centres until one run takes about `seconds`; returns (centres/s, n, seconds, next start)."""
+    n = 8
+    while True:
+        n = int(min(n, len(order) - start))
         t0 = time.perf_counter()
         run(order[start:start + n])
         dt = time.perf_counter() - t0
         start += n
-        if dt >= 0.7 * args.cpu_seconds or start >= system.n_atoms:
-            break
-        n = int(n * min(8.0, args.cpu_seconds / max(dt, 1e-3)))
-    print(json.dumps({"value": n / dt, "n": n, "seconds": dt}))
+        if dt >= 0.7 * seconds or start >= len(order):
+            return n / dt, n, dt, start
+        n = int(n * min(8.0, seconds / max(dt, 1e-3)))
+
+
+def _time_pool(argv, system, spline, order, rate1, procs, seconds):
+    """Runs the same oracle pass over a process pool (spawned, one thread each) on a sample sized from the
+    single-thread rate; returns (centres/s, n, wall seconds)."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    n = int(min(len(order), max(4 * procs, rate1 * procs * seconds)))
+    chunk = max(1, n // (6 * procs))
+    tasks = [order[k:k + chunk] for k in range(0, n, chunk)]
+    with mp.get_context("spawn").Pool(procs, initializer=_pool_init, initargs=(argv, system, spline)) as pool:
+        pool.map(_pool_task, [np.array([0, 1])] * procs, chunksize=1)  # every process is up and warm
+        t0 = time.perf_counter()
+        done = sum(pool.imap_unordered(_pool_task, tasks, chunksize=1))
+        dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def host_cpu():
+    """(logical cores usable by this process, CPU model name)."""
+    import platform
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model or platform.processor() or platform.machine()
+
+
+def cpu_worker(args, argv):
+    """Times the FP64 oracle on bounded, seeded samples of centres of the workload: exact radial integrals on one
+    host thread and on every host core (a spawned process pool, one thread per process), and the paper's spline
+    optimisation (FP64 clamped cubic spline of the same integrals) on every core."""
+    import numpy as np
+
+    from oracle import radial as oradial
+    from oracle import soap as osoap
+
+    system = make_system(args.config, 0)
+    system.hypers = dict(system.hypers, basis=args.basis)
+    h = osoap.Hypers(**system.hypers)
+    order = np.random.default_rng(123).permutation(system.n_atoms)
+    cores, model = host_cpu()
+    per_mode = args.cpu_seconds / 3.0
+    run = oracle_step_fn(args, system, h)
+    run(order[:2])  # first call builds the oracle's per-(a, b) 1F1 switch points
+    rate1, n1, dt1, _ = _time_serial(run, order, 2, per_mode)
+    modes = [{"radial": "exact 1F1", "cores": 1, "value": rate1, "centres": n1, "seconds": dt1}]
+    ratep, npool, dtp = _time_pool(argv, system, None, order, rate1, cores, per_mode) if cores > 1 else (rate1, n1, dt1)
+    modes.append({"radial": "exact 1F1", "cores": cores, "value": ratep, "centres": npool, "seconds": dtp})
+    if args.basis == "gto":
+        spline = oradial.RadialSpline(h.r_cut, h.sigma, h.n_max, h.l_max, accuracy=1e-8, orthonormal=h.orthonormal)
+        srun = oracle_step_fn(args, system, h, lambda r, d=False: spline(r, d))
+        srun(order[:2])
+        rate_s1 = _time_serial(srun, order, 2, 0.25 * per_mode)[0]
+        rs, ns, dts = _time_pool(argv, system, spline, order, rate_s1, cores, per_mode) if cores > 1 else \
+            _time_serial(srun, order, 2, per_mode)[:3]
+        modes.append({"radial": f"FP64 spline ({spline.M} intervals, midpoint error <= 1e-8)", "cores": cores,
+                      "value": rs, "centres": ns, "seconds": dts})
+    print(json.dumps({"modes": modes, "nproc": cores, "cpu_model": model}))
 
 
 def gpr_text(args):
@@ -282,7 +366,7 @@ def oracle_gpr_model(args, system, h):
     return pm, h.species_index(system.species[idx]), x
 
 
-def oracle_gpr_step(args, system, h, model, centres):
+def oracle_gpr_step(args, system, h, model, centres, radial_fn=None):
     """c, packed p, the GPR energies (and with --gradients dE/dp, forces and virial) of the sampled centres."""
     import numpy as np
 
@@ -292,95 +376,95 @@ def oracle_gpr_step(args, system, h, model, centres):
     pm, ms, x = model
     centres = np.asarray(centres)
     cs = h.species_index(system.species[centres])
-    p = osoap.power_spectrum(osoap.spherical_expansion(system, h, centres=centres), h, "packed").reshape(centres.size, -1)
+    p = osoap.power_spectrum(osoap.spherical_expansion(system, h, centres=centres, radial_fn=radial_fn), h,
+                             "packed").reshape(centres.size, -1)
     E = ogpr.energies(p, cs, pm, ms, x, args.zeta)
     if args.gradients:
         g = ogpr.grad_p(p, cs, pm, ms, x, args.zeta)
-        return E, osoap.energy_gradients(system, h, None, centres=centres, grad_p=g)
+        return E, osoap.energy_gradients(system, h, None, centres=centres, grad_p=g, radial_fn=radial_fn)
     return E
 
 
-def cpu_baseline(args, cores=1):
-    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores),
-               CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--config", args.config, "--layout", args.layout,
-           "--cpu-seconds", str(args.cpu_seconds), "--basis", args.basis, "--gpr", str(args.gpr), "--zeta", str(args.zeta),
-           "--lambda-soap", str(args.lambda_soap)] + (["--gradients"] if args.gradients else []) + \
-          (["--expansion-only"] if args.expansion_only else [])
-    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+def cpu_baseline(args):
+    """The oracle timed on the host cores in a subprocess with no GPU visible (one thread per process)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    argv = ["--config", args.config, "--layout", args.layout, "--cpu-seconds", str(args.cpu_seconds), "--basis",
+            args.basis, "--gpr", str(args.gpr), "--zeta", str(args.zeta), "--lambda-soap", str(args.lambda_soap)] + \
+        (["--gradients"] if args.gradients else []) + (["--expansion-only"] if args.expansion_only else [])
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker"] + argv
+    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1200)
     if res.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": res.stderr[-300:]}
+        return {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "error": res.stderr[-300:]}
     d = json.loads(res.stdout.strip().splitlines()[-1])
-    return {"value": d["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{d['n']} seeded random centres of the {args.config} workload (neighbours + exact {'1F1' if args.basis == 'gto' else 'DVR'} coefficients"
-                      f"{'' if args.expansion_only else ' + ' + args.layout + ' power spectrum'}"
-                      f"{gpr_text(args)}{' + forces and virial' if args.gradients else ''}, FP64 numpy), "
-                      f"{d['seconds']:.1f} s on one host thread"}
+    modes = d["modes"]
+    main = modes[1]  # exact integrals on every host core
+    what = (f"neighbours + {'1F1' if args.basis == 'gto' else 'DVR'} coefficients"
+            f"{'' if args.expansion_only else ' + ' + args.layout + ' power spectrum'}"
+            f"{gpr_text(args)}{' + forces and virial' if args.gradients else ''}, FP64 numpy")
+    return {"value": main["value"], "unit": UNIT, "cores": main["cores"], "kind": "oracle",
+            "sample": f"{main['centres']} seeded random centres of the {args.config} workload ({what}), exact radial "
+                      f"integrals, {main['seconds']:.1f} s on {main['cores']} host processes of one thread each",
+            "host": {"nproc": d["nproc"], "cpu_model": d["cpu_model"]},
+            "modes": [{k: m[k] for k in ("radial", "cores", "value", "centres", "seconds")} for m in modes]}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (exact radial integrals) on every host core, a spawned process pool of
+    one thread each, each step a bounded seeded sample of the same workload."""
     rank, world, _ = dist_init(args)
     if rank != 0:
         return 0
+    import multiprocessing as mp
+
     import numpy as np
 
     from oracle import soap as osoap
 
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"  # inherited by the spawned processes
     system = make_system(args.config, 0)
     system.hypers = dict(system.hypers, basis=args.basis)
     h = osoap.Hypers(**system.hypers)
-    rng = np.random.default_rng(7)
-    order = rng.permutation(system.n_atoms)
-    w = None
-    if args.gradients:
-        from synth import linear_weights
+    order = np.random.default_rng(7).permutation(system.n_atoms)
+    cores, model = host_cpu()
+    argv = ["--config", args.config, "--layout", args.layout, "--basis", args.basis, "--gpr", str(args.gpr), "--zeta",
+            str(args.zeta), "--lambda-soap", str(args.lambda_soap)] + (["--gradients"] if args.gradients else []) + \
+        (["--expansion-only"] if args.expansion_only else [])
+    with mp.get_context("spawn").Pool(cores, initializer=_pool_init, initargs=(argv, system, None)) as pool:
+        pool.map(_pool_task, [np.array([0, 1])] * cores, chunksize=1)
+        t0 = time.perf_counter()
+        probe = sum(pool.map(_pool_task, [order[2 + 2 * k:4 + 2 * k] for k in range(cores)], chunksize=1))
+        per = (time.perf_counter() - t0) / probe  # wall seconds per centre with every core busy
+        budget = 150.0
+        per_step = max(cores, int(budget / max(per, 1e-6) / (args.steps + args.warmup)))
+        cursor = 2 + 2 * cores
 
-        w = linear_weights(h.n_species, h.n_features("packed"), seed=4)
+        def step():
+            nonlocal cursor
+            idx = np.take(order, np.arange(cursor, cursor + per_step), mode="wrap")
+            cursor += per_step
+            chunk = max(1, -(-per_step // (4 * cores)))
+            return sum(pool.imap_unordered(_pool_task, [idx[k:k + chunk] for k in range(0, per_step, chunk)],
+                                           chunksize=1))
 
-    gpr_model = oracle_gpr_model(args, system, h) if args.gpr else None
-
-    def run(idx):
-        if args.lambda_soap >= 0:
-            from oracle import lambda_soap as ols
-
-            return ols.equivariants(osoap.spherical_expansion(system, h, centres=idx), h, args.lambda_soap)
-        if gpr_model is not None:
-            return oracle_gpr_step(args, system, h, gpr_model, idx)
-        if w is not None:
-            return osoap.energy_gradients(system, h, w, centres=idx)
-        c = osoap.spherical_expansion(system, h, centres=idx)
-        return c if args.expansion_only else osoap.power_spectrum(c, h, args.layout)
-
-    run(order[:2])
-    t0 = time.perf_counter()
-    run(order[:4])
-    per = (time.perf_counter() - t0) / 4
-    budget = 150.0
-    per_step = max(1, int(budget / max(per, 1e-6) / (args.steps + args.warmup)))
-    cursor = 2
-
-    def step():
-        nonlocal cursor
-        idx = np.take(order, np.arange(cursor, cursor + per_step), mode="wrap")
-        cursor += per_step
-        run(idx)
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    value = per_step * args.steps / dt
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        done = 0
+        for _ in range(args.steps):
+            done += step()
+        dt = time.perf_counter() - t0
+    value = done / dt
     sample = (f"{per_step} seeded random centres per step of the {args.config} workload (neighbours + exact "
               f"{'1F1' if args.basis == 'gto' else 'DVR'} coefficients{'' if args.expansion_only else ' + ' + args.layout + ' power spectrum'}"
               f"{gpr_text(args)}{' + forces and virial' if args.gradients else ''}, "
-              f"FP64 numpy), one host thread")
+              f"FP64 numpy), {cores} host processes of one thread each")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}", "global_batch": per_step},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "host": {"nproc": cores, "cpu_model": model}},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -551,11 +635,13 @@ def run_ours(args):
         Q = calc.n_species * calc.n_max
         flops = 10.0 * calc.n_max * n_lm * n_pairs + 2.0 * Q * Q * n_lm * N
         sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
-        alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock, TFLOP/s
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock, TFLOP/s
         achieved = flops / (t_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak, "traffic": None, "algorithmic_flops_per_launch": flops,
-                    "peak_source": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+                    "peak_source": f"FP32 FMA peak from unit counts: {n_sm} SMs (device properties) x 128 lanes x "
+                                   "2 flop x max SM clock"}
     else:
         achieved = (alg / (t_ms * 1e-3) / 1e9) if alg else None
         traffic_known = (kernel.startswith("k_expansion<fused") and args.config == "batch" and args.ps == "fp32"
@@ -752,7 +838,7 @@ def measure_e2e(args, calc, system, dev, stream, ps, coeffs, rg, steps=None, wei
 def main(argv=None):
     args = parse_args(argv)
     if args.cpu_worker:
-        cpu_worker(args)
+        cpu_worker(args, [a for a in (sys.argv[1:] if argv is None else argv) if a != "--cpu-worker"])
         return 0
     if args.impl == "reference":
         return run_reference(args)

@@ -38,7 +38,8 @@ extern "C" {
 #endif
 
 #define RASCAL_OK 0
-#define RASCAL_E_ARG (-1)         /* invalid argument (null pointer, out-of-range hyper, unknown species) */
+#define RASCAL_E_ARG (-1)         /* invalid argument (null pointer, out-of-range hyper, unknown species,
+                                     non-finite position) */
 #define RASCAL_E_CAPACITY (-2)    /* output buffer too small; the required size is reported */
 #define RASCAL_E_CUDA (-3)        /* a CUDA runtime call failed */
 #define RASCAL_E_UNSUPPORTED (-4) /* valid input outside what the kernels support (e.g. |shift| > 511) */
@@ -110,6 +111,7 @@ typedef struct {
     int spline_intervals;        /* M chosen for the radial table */
     double spline_error;         /* max |FP64 spline - exact| at interval midpoints, over all (n, l) */
     double spline_error_fp32;    /* the same for the FP32 coefficients the kernels read */
+    int64_t scratch_bytes;       /* device bytes held by the context's scratch arenas now (they grow on demand) */
 } rascal_info_t;
 
 /* Thread-local message of the last failed call on this thread ("" if none). Never NULL. */
@@ -153,14 +155,17 @@ int rascal_neighbours(rascal_ctx* ctx, const rascal_system* sys, int64_t capacit
  * rascal_neighbours_static_limit() bytes (32 MiB) instead of the context's scratch arena; it calls no cudaMalloc,
  * cudaFree or other allocating routine.
  *   - The array is part of the library's device image: every GPU that loads the library holds it until exit.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress, with that device
- *     current) and caches it; make that first call before any stream capture.
+ *   - rascal_create looks up the array's device address for the context's device (cudaGetSymbolAddress, with
+ *     that device current) and caches it, so the calls themselves do no lookup. Make the call with the context's
+ *     device current; otherwise it returns RASCAL_E_ARG.
  *   - All calls share the one array and it keeps the last call's contents (what must start at zero is cleared
  *     on every call). Calls that overlap on the GPU (other streams, other contexts, other host threads) race on
  *     it: serialise them.
  *   - Limits: a system needing more scratch than the array (about 116 bytes per atom plus 360 per structure:
- *     some 280k atoms in one cell) is refused with RASCAL_E_UNSUPPORTED before anything runs; so is a centre with
- *     more than 256 neighbours, which rascal_neighbours sorts in an allocated overflow buffer.
+ *     some 280k atoms in one cell) is refused with RASCAL_E_UNSUPPORTED before anything runs. A centre with more
+ *     than 256 neighbours (rascal_neighbours sorts those in an allocated overflow buffer) is also refused with
+ *     RASCAL_E_UNSUPPORTED, but only once the counting pass has run: d_offsets and *n_pairs are then already
+ *     written, and this check comes before the capacity check.
  * Synchronises the stream once, like rascal_neighbours. */
 int rascal_neighbours_noalloc(rascal_ctx* ctx, const rascal_system* sys, int64_t capacity, int64_t* d_offsets,
                               int* d_nbr_j, int* d_shift, float* d_rij, int64_t* n_pairs);

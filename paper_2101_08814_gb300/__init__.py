@@ -137,6 +137,12 @@ class SoapCalculator:
     def n_features(self, layout="packed"):
         return int(self.info["features_packed" if layout == "packed" else "features_full"])
 
+    def scratch_bytes(self):
+        """Device bytes the context's scratch arenas hold now (they grow on demand and are kept)."""
+        info = _lib.Info()
+        _lib.check(_lib.lib().rascal_info(self._ctx, C.byref(info)))
+        return int(info.scratch_bytes)
+
     def sync(self):
         self._bind_stream()
         _lib.check(_lib.lib().rascal_sync(self._ctx))

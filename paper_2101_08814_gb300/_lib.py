@@ -65,6 +65,7 @@ class Info(C.Structure):
         ("spline_intervals", C.c_int),
         ("spline_error", C.c_double),
         ("spline_error_fp32", C.c_double),
+        ("scratch_bytes", C.c_int64),
     ]
 
 

@@ -29,6 +29,7 @@ enum : unsigned {
     kFlagBadOffsets = 1u << 4,  // structure offsets not increasing / out of range
     kFlagTimeout = 1u << 5,     // a bounded wait on a tensor-core completion barrier ran out
     kFlagSelection = 1u << 6,   // a selected feature index is outside the packed feature vector
+    kFlagNonFinite = 1u << 7,   // an atom position is NaN or infinite
 };
 
 // -------------------------------------------------------------------------------------------- status
@@ -190,6 +191,8 @@ int power_spectrum_setup(rascal_ctx* ctx);
 // BF16 / TF32x3 power spectrum of given coefficients [n][Q][n_lm] by the fused kernel's tensor-core Gram
 int power_spectrum_tc(rascal_ctx* ctx, int64_t n_centres, const float* d_coeffs, int precision, int layout, float* d_ps);
 int gradients_setup(rascal_ctx* ctx);
+// caches the device address of the no-allocation neighbour scratch for ctx->device (neighbours.cu)
+int nbr_static_prepare(rascal_ctx* ctx);
 void lsoap_free(rascal_ctx* ctx);
 
 }  // namespace rascal

@@ -57,6 +57,7 @@ int check_flags(rascal_ctx* ctx) {
     RASCAL_CUDA(cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned), ctx->stream));
     if (f & kFlagSpecies) return set_error(RASCAL_E_ARG, "an atom's species label is not in the hypers' species list");
     if (f & kFlagBadOffsets) return set_error(RASCAL_E_ARG, "structure offsets are not non-decreasing within [0, n_atoms]");
+    if (f & kFlagNonFinite) return set_error(RASCAL_E_ARG, "an atom position is not finite");
     if (f & kFlagGeometry) return set_error(RASCAL_E_GEOMETRY, "singular cell or coincident atoms (r < 1e-6 A)");
     if (f & kFlagThinCell) return set_error(RASCAL_E_UNSUPPORTED, "a cell is thinner than r_cut/64 along some axis");
     if (f & kFlagShiftRange) return set_error(RASCAL_E_UNSUPPORTED, "a periodic shift exceeds |n| <= 511");
@@ -550,6 +551,7 @@ static int create_impl(const rascal_hypers* h, void* stream, rascal_ctx** out) {
     if ((st = power_spectrum_setup(ctx))) return st;
     if ((st = gradients_setup(ctx))) return st;
     if ((st = mlp_setup(ctx))) return st;
+    if ((st = nbr_static_prepare(ctx))) return st;
     RASCAL_CUDA(cudaStreamSynchronize(ctx->stream));
     return RASCAL_OK;
 }
@@ -590,6 +592,7 @@ extern "C" int rascal_info(const rascal_ctx* ctx, rascal_info_t* o) {
     o->spline_intervals = ctx->M;
     o->spline_error = ctx->spline_error;
     o->spline_error_fp32 = ctx->spline_error_fp32;
+    o->scratch_bytes = (int64_t)(ctx->scratch.bytes + ctx->scratch2.bytes + ctx->scratch_w.bytes + ctx->scratch_sel.bytes);
     return RASCAL_OK;
 }
 

@@ -11,7 +11,7 @@
 // centres are first bucketed by species (k_gpr_count, k_gpr_scatter: a stable counting sort on the device).
 //   k_gpr_kernel: D[128 centres][<= 512 sparse points] = p_rows . M^T over the features, A rows gathered from the
 //     feature matrix by cp.async (16-byte copies, zero-filled past the end), B = M^ rows (TF32-rounded at model
-//     creation); 4-stage shared-memory pipeline, one thread issues the MMAs, completion per stage on mbarriers.
+//     creation); 5-stage shared-memory pipeline (kGprStages), one thread issues the MMAs, completion per stage on mbarriers.
 //     Epilogue (TMEM -> registers): the row norms (accumulated from the staged A tiles), k^zeta, E partials and the
 //     per-(centre, point) factor W = x zeta k^(zeta-1), stored for the gradient GEMM.
 //   k_gpr_finish: per structure, E_i summed over the passes, FP64 structure energies, zeta E_i / |p_i|^2 (the

@@ -139,6 +139,9 @@ __global__ void k_atom_bin(int n_atoms, int n_s, int64_t nbins_cap, const int* _
     const int s = find_structure(offs, n_s, i);
     StructInfo& S = info[s];
     const double r[3] = {pos[3 * (int64_t)i], pos[3 * (int64_t)i + 1], pos[3 * (int64_t)i + 2]};
+    // a non-finite position is reported; the clamps below keep its bin and wrap count in range, and its FP32
+    // thresholds become NaN, so no pair of its structure is accepted before the call returns the error
+    if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]))) atomicOr(flags, kFlagNonFinite);
     const int lab = species[i];
     int a = (lab >= 0 && lab < 256) ? lut[lab] : -1;
     if (a < 0) {
@@ -580,8 +583,8 @@ extern "C" int rascal_neighbours(rascal_ctx* ctx, const rascal_system* sys, int6
 // ---------------------------------------------------------------------------------------------------------
 // Neighbour search that allocates nothing: the same kernels as rascal_neighbours, with all scratch carved out of
 // one file-scope device array. The array is a module global, so every GPU that loads the library holds it until
-// the process exits. Its device address is looked up once per device (cudaGetSymbolAddress with that device
-// current, on the first call made on it) and cached; all calls on a device share the array.
+// the process exits. Its device address is looked up per device (cudaGetSymbolAddress with that device current)
+// when a context is created on it, and cached; all calls on a device share the array.
 // ---------------------------------------------------------------------------------------------------------
 namespace rascal {
 
@@ -591,20 +594,33 @@ constexpr int kMaxDevices = 64;
 static void* g_nbr_scratch_addr[kMaxDevices];
 static std::mutex g_nbr_scratch_mu;
 
-static int static_nbr_scratch(void** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return set_error(RASCAL_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+// Caches the device address of the array for ctx->device, which must be the current device. Called by
+// rascal_create, so the lookup (which may load the module and reserve the array) happens before any step loop.
+int nbr_static_prepare(rascal_ctx* ctx) {
+    const int dev = ctx->device;
     if (dev < 0 || dev >= kMaxDevices) return set_error(RASCAL_E_UNSUPPORTED, "device ordinal %d above %d", dev, kMaxDevices - 1);
     std::lock_guard<std::mutex> lock(g_nbr_scratch_mu);
     if (!g_nbr_scratch_addr[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_nbr_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_nbr_scratch);
         if (e != cudaSuccess || !p)
             return set_error(RASCAL_E_CUDA, "cudaGetSymbolAddress of the static neighbour scratch: %s", cudaGetErrorString(e));
         g_nbr_scratch_addr[dev] = p;
     }
-    *out = g_nbr_scratch_addr[dev];
+    return RASCAL_OK;
+}
+
+// The cached address for the context's device. The kernels run on ctx->stream, which belongs to ctx->device, so a
+// call made while another device is current is refused rather than handed another GPU's copy of the array.
+static int static_nbr_scratch(const rascal_ctx* ctx, void** out) {
+    int cur = -1;
+    const cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return set_error(RASCAL_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (cur != ctx->device)
+        return set_error(RASCAL_E_ARG, "the current device (%d) is not the context's device (%d)", cur, ctx->device);
+    std::lock_guard<std::mutex> lock(g_nbr_scratch_mu);
+    *out = g_nbr_scratch_addr[ctx->device];
+    if (!*out) return set_error(RASCAL_E_CUDA, "the static neighbour scratch of device %d was not prepared", ctx->device);
     return RASCAL_OK;
 }
 
@@ -639,7 +655,7 @@ extern "C" int rascal_neighbours_noalloc(rascal_ctx* ctx, const rascal_system* s
                          "(about 116 bytes per atom and 360 per structure): use rascal_neighbours",
                          bytes, kStaticNbrScratchBytes);
     void* base = nullptr;
-    if ((st = static_nbr_scratch(&base))) return st;
+    if ((st = static_nbr_scratch(ctx, &base))) return st;
     Carver cv(base);
     StructInfo* info = cv.take<StructInfo>(n_s);
     int* nbins = cv.take<int>(n_s + 1);
@@ -688,12 +704,13 @@ extern "C" int rascal_neighbours_noalloc(rascal_ctx* ctx, const rascal_system* s
     const int64_t P = ctx->h_pinned[0];
     const int maxc = *reinterpret_cast<int*>(ctx->h_pinned + 1);
     *n_pairs = P;
-    if (P > capacity) return set_error(RASCAL_E_CAPACITY, "pair capacity %lld < required %lld", (long long)capacity, (long long)P);
-    if (P == 0) return RASCAL_OK;
-    if (!d_nbr_j || !d_shift || !d_rij) return set_error(RASCAL_E_ARG, "NULL pair output arrays");
+    // checked before the capacity, so that a caller who resizes after RASCAL_E_CAPACITY is not refused afterwards
     if (maxc > kNoallocCap)
         return set_error(RASCAL_E_UNSUPPORTED, "a centre has %d neighbours; the no-allocation entry point sorts at most %d "
                          "per centre (rascal_neighbours has no such limit)", maxc, kNoallocCap);
+    if (P > capacity) return set_error(RASCAL_E_CAPACITY, "pair capacity %lld < required %lld", (long long)capacity, (long long)P);
+    if (P == 0) return RASCAL_OK;
+    if (!d_nbr_j || !d_shift || !d_rij) return set_error(RASCAL_E_ARG, "NULL pair output arrays");
     k_pairs<true, kNoallocCap><<<pair_blocks, kPairWarps * 32, 0, stream>>>(N, sys->d_positions, info, binbase, bin_start, sorted_hi,
                                                                atom_struct, atom_cell, atom_wrap, atom_hi, atom_lo, rc2,
                                                                nbins_cap, d_offsets, nullptr, d_nbr_j, d_shift,

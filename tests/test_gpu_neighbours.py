@@ -5,7 +5,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 from oracle.neighbours import neighbour_list  # noqa: E402
-from synth import System, config_batch, config_tiny, small_cell_system  # noqa: E402
+from synth import System, config_batch, config_tiny, random_cell_atoms, small_cell_system  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -135,3 +135,59 @@ def test_capacity_and_unknown_species_errors(rg):
     # the context stays usable after an error
     pl = calc.neighbours(ds)
     assert pl.n_pairs == P.value
+
+
+def test_centres_with_more_than_128_neighbours(rg):
+    # 532 atoms in a 16 A cell with r_cut 7: 164..202 neighbours per centre, more than a warp sorts in shared
+    # memory, so every segment goes through the global overflow sort
+    L, n = 16.0, 532
+    rng = np.random.Generator(np.random.PCG64(51))
+    pos = random_cell_atoms(n, np.eye(3) * L, 1.2, rng)
+    s = System(pos, np.full(n, 6, np.int32), (np.eye(3) * L)[None], np.ones((1, 3), np.int32), np.array([0, n], np.int32),
+               dict(r_cut=7.0, sigma=0.5, n_max=2, l_max=1, smooth_width=0.5, species=[6]))
+    _, _, gpu = _gpu_pairs(rg, s)
+    ref = neighbour_list(s, 7.0)
+    assert np.diff(ref["offsets"]).min() > 128
+    _assert_same(gpu, ref)
+
+
+def _expect_status(rg, system, code, text):
+    calc = rg.SoapCalculator(**system.hypers)
+    with pytest.raises(rg.RascalError) as e:
+        calc.neighbours(rg.DeviceSystem.from_numpy(system))
+    assert e.value.code == code, (e.value.code, str(e.value))
+    assert text in str(e.value)
+    # the context keeps working after the error
+    t = config_tiny()
+    calc2 = rg.SoapCalculator(**t.hypers)
+    assert calc2.neighbours(rg.DeviceSystem.from_numpy(t)).n_pairs > 0
+
+
+HYP = dict(r_cut=5.0, sigma=0.5, n_max=2, l_max=1, smooth_width=0.5, species=[14])
+
+
+def _one_cell(pos, cell):
+    pos = np.asarray(pos, np.float64)
+    return System(pos, np.full(len(pos), 14, np.int32), np.asarray(cell, np.float64)[None], np.ones((1, 3), np.int32),
+                  np.array([0, len(pos)], np.int32), dict(HYP))
+
+
+def test_coincident_atoms_are_a_geometry_error(rg):
+    pos = [[1.0, 2.0, 3.0], [4.0, 4.0, 4.0], [1.0, 2.0, 3.0]]
+    _expect_status(rg, _one_cell(pos, np.eye(3) * 12.0), rg._lib.RASCAL_E_GEOMETRY, "coincident")
+    # an atom on top of another atom's periodic image is coincident too
+    pos = [[1.0, 2.0, 3.0], [13.0, 2.0, 3.0]]
+    _expect_status(rg, _one_cell(pos, np.eye(3) * 12.0), rg._lib.RASCAL_E_GEOMETRY, "coincident")
+
+
+def test_singular_and_too_thin_cells_are_refused(rg):
+    singular = np.array([[10.0, 0.0, 0.0], [0.0, 10.0, 0.0], [5.0, 5.0, 0.0]])
+    _expect_status(rg, _one_cell([[1.0, 1.0, 1.0], [3.0, 2.0, 1.0]], singular), rg._lib.RASCAL_E_GEOMETRY, "singular")
+    thin = np.diag([10.0, 10.0, 0.05])  # perpendicular width 0.05 < r_cut / 64
+    _expect_status(rg, _one_cell([[1.0, 1.0, 0.01], [3.0, 2.0, 0.02]], thin), rg._lib.RASCAL_E_UNSUPPORTED, "thinner")
+
+
+def test_non_finite_positions_are_refused(rg):
+    for bad in (np.nan, np.inf, -np.inf):
+        pos = [[1.0, 2.0, 3.0], [4.0, bad, 4.0], [6.0, 6.0, 6.0]]
+        _expect_status(rg, _one_cell(pos, np.eye(3) * 12.0), rg._lib.RASCAL_E_ARG, "not finite")

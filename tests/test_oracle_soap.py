@@ -202,3 +202,45 @@ def test_include_center_adds_l0_term_only():
     assert np.all(d[..., 1:] == 0.0)
     I0 = radial.integrals(np.array([0.0]), h0.r_cut, h0.sigma, 3, 2)[0][:, 0]
     assert np.allclose(d[0, 0, :, 0], I0 / (2 * sqrt(pi)))
+
+
+def test_three_species_power_spectrum_matches_ylm_free_bruteforce():
+    # species channel of Eq. spherical_expansion_coefficients_gaussians: neighbour j adds only to block a_j, with
+    # blocks ordered by the sorted labels (the labels are given unsorted); the brute force assigns each neighbour's
+    # radial row by its own species and never forms c, so a term routed to the wrong block (e.g. the centre's
+    # species) changes the off-diagonal species blocks of p and fails here
+    hyp = dict(r_cut=4.5, sigma=0.45, n_max=3, l_max=4, smooth_width=0.5, species=[8, 1, 6])
+    s = small_cell_system(seed=17, n_atoms=9, L=4.6, hypers=hyp)
+    assert set(np.unique(s.species)) == {1, 6, 8}
+    h = soap.Hypers(**s.hypers)
+    for centre in range(s.n_atoms):
+        p = soap.power_spectrum(soap.spherical_expansion(s, h, centres=[centre]), h, "full")[0]
+        ref = soap.power_spectrum_bruteforce(s, h, centre)
+        assert np.max(np.abs(ref)) > 0.0
+        assert np.allclose(p, ref, rtol=0.0, atol=1e-12 * np.max(np.abs(ref))), centre
+
+
+def test_two_species_single_neighbour_fills_only_its_own_block():
+    # one neighbour of label 8 around a centre of label 1, hypers listing the labels unsorted: c is non-zero only in
+    # block a_j = 2 (sorted labels 1, 6, 8), and p only in the (a_j, a_j) block, where it takes the closed form
+    # f^2 I_n1l I_n2l sqrt(2l+1)/(4 pi) of a single neighbour
+    h = soap.Hypers(r_cut=5.0, sigma=0.5, n_max=4, l_max=3, species=[8, 1, 6])
+    d = np.array([0.4, -1.9, 1.3])
+    s = _two_atoms(d, species=(1, 8))
+    c = soap.spherical_expansion(s, h, centres=[0])[0]            # [S, n, lm]
+    r = np.linalg.norm(d)
+    f = soap.cutoff(r, 5.0, 0.5)
+    I = radial.integrals(np.array([r]), 5.0, 0.5, 4, 3)[0]
+    Y = ylm.real_ylm(d[None], 3)[0]
+    lidx = np.array([l for l in range(4) for _ in range(2 * l + 1)])
+    assert np.all(c[0] == 0.0) and np.all(c[1] == 0.0)
+    assert np.allclose(c[2], f * I[:, lidx] * Y[None, :], atol=1e-15)
+    p = soap.power_spectrum(c[None], h, "full")[0]                 # [l, Q, Q]
+    n = 4
+    for l in range(4):
+        blk = np.zeros((12, 12))
+        blk[2 * n:3 * n, 2 * n:3 * n] = f * f * np.outer(I[:, l], I[:, l]) * sqrt(2 * l + 1) / (4 * pi)
+        assert np.allclose(p[l], blk, atol=1e-14)
+    # the centre of label 8 seen from the other side: its neighbour (label 1) fills block 0 only
+    c1 = soap.spherical_expansion(s, h, centres=[1])[0]
+    assert np.any(c1[0] != 0.0) and np.all(c1[1] == 0.0) and np.all(c1[2] == 0.0)
