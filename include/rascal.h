@@ -133,6 +133,13 @@ int rascal_info(const rascal_ctx* ctx, rascal_info_t* out);
  * label, degenerate geometry, ...) into a status. */
 int rascal_sync(rascal_ctx* ctx);
 
+/* Test hook for the failure path of the tensor-core kernels (no counterpart in the paper): sets the iteration bound
+ * of their bounded mbarrier waits (0 restores the built-in bound of 2^22 polls). With a bound of 1 a wait for an MMA
+ * batch gives up almost at once: the kernel raises the timeout flag, every role leaves its loop, the MMAs already
+ * issued are drained with the built-in bound before the tensor memory is freed, and the next synchronising call
+ * returns RASCAL_E_TIMEOUT. The outputs of that call are then incomplete; the context stays usable. */
+int rascal_set_wait_limit(rascal_ctx* ctx, unsigned limit);
+
 /* Periodic neighbour list (Appendix B). For every atom i (all structures, in atom order) the pairs (j, n) with
  * |r_j - r_i + n H| < r_cut, (j, n) != (i, 0), sorted by (j, n1, n2, n3). The inclusion test is bit-exact with
  * the FP64 definition d = (r_j - r_i) + ((n1 h1 + n2 h2) + n3 h3), d.d = (dx dx + dy dy) + dz dz < r_cut^2.
@@ -176,6 +183,16 @@ size_t rascal_neighbours_static_limit(void);
  * list made by rascal_neighbours for the same system. d_coeffs: [n_atoms][n_species][n_max][(l_max+1)^2]. */
 int rascal_spherical_expansion(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets,
                                const int* d_nbr_j, const float* d_rij, float* d_coeffs);
+
+/* Test hook for small cases: the per-pair feature gradient written out (Appendix B, Eq. energy-derivative, and
+ * Eq. spherical_expansion_coefficients_gaussians). For pair p with r = r_ji = d_rij[p] (the (x, y, z, |r|) rows of a
+ * pair list made by rascal_neighbours) it writes
+ *   d_dc [n_pairs][3][n_max][(l_max+1)^2] float32:  d/dr_x [ f_cut(r) I^o_nl(r) Y_lm(r^) ],
+ * the derivative of that pair's term in c^i_{a_j n l m} with respect to the x-th component of r_ji (its species
+ * block is a_j; the other blocks do not depend on this pair). Radial values come from the context's radial mode.
+ * rascal_gradients never forms this tensor (it recomputes it per pair inside the contraction); this call exists to
+ * check it. n_pairs <= 2^20, else RASCAL_E_ARG. */
+int rascal_debug_pair_gradients(rascal_ctx* ctx, int64_t n_pairs, const float* d_rij, float* d_dc);
 
 /* Power spectrum (Eq. nu2-basis-coupled) of n_centres coefficient blocks. precision: RASCAL_PS_FP32 or
  * RASCAL_PS_BF16 (tensor cores, inputs rounded to bfloat16, FP32 accumulation). layout: RASCAL_LAYOUT_*. */

@@ -189,15 +189,17 @@ def adjoint_coefficients(c, hypers: Hypers, grad_p_packed):
     return chat.reshape(c.shape)
 
 
-def energy_gradients(system, hypers: Hypers, weights, radial_fn=None, centres=None, grad_p=None):
+def energy_gradients(system, hypers: Hypers, weights, radial_fn=None, centres=None, grad_p=None, nl=None):
     """Forces F = -dE/dr [N,3] and virial V = sum_pairs dE/dr_ji (x) r_ji [n_structures,3,3] for the linear model.
 
     dE_i/dr_ji = sum_{n l m} chat^i_{a_j n l m} grad_r [f(r) I_nl(r) Y_lm(r^)], evaluated exactly per pair.
     centres: optional subset of centre atoms; the result is then the gradient of sum_{i in centres} E_i only.
     grad_p: optional dE/dp per centre [n_centres, F] (PACKED) in place of the linear model's weights[a_i], for any
-    energy that depends on the atoms through the power spectrum only (Eq. gpr-force-order)."""
+    energy that depends on the atoms through the power spectrum only (Eq. gpr-force-order).
+    nl: optional neighbour list of those centres from neighbour_list (saves recomputing it)."""
     h = hypers
-    nl = neighbour_list(system, h.r_cut, centres)
+    if nl is None:
+        nl = neighbour_list(system, h.r_cut, centres)
     cidx = nl["centres"]
     c = spherical_expansion(system, h, nl=nl, radial_fn=radial_fn)
     a_all = h.species_index(system.species)

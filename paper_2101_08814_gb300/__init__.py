@@ -253,6 +253,19 @@ class SoapCalculator:
                                                _ptr(forces), _ptr(virial)))
         return forces, virial
 
+    def debug_pair_gradients(self, rij):
+        """d/dr_ji of each pair's term f_cut I^o_nl Y_lm: [P, 3, n_max, (l_max+1)^2] float32 (a test hook)."""
+        import torch
+
+        self._bind_stream()
+        rij = rij.contiguous()
+        if rij.dtype != torch.float32 or rij.dim() != 2 or rij.shape[1] != 4 or rij.device.type != "cuda":
+            raise ValueError("rij must be a float32 [P, 4] CUDA tensor (x, y, z, r)")
+        P = int(rij.shape[0])
+        out = torch.empty((P, 3, self.n_max, (self.l_max + 1) ** 2), dtype=torch.float32, device=self.device)
+        _lib.check(_lib.lib().rascal_debug_pair_gradients(self._ctx, P, _ptr(rij), _ptr(out)))
+        return out
+
     def lambda_soap_size(self, lam: int):
         """(number of (l1, l2) pairs, features per centre) of the rank-lam equivariants."""
         n_pairs, feat = C.c_int(), C.c_int64()

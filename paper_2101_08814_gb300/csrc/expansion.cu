@@ -74,7 +74,9 @@ struct ExpArgs {
 __device__ inline float cutoff_fp32(float r, float r_cut, float w) {
     if (r <= r_cut - w) return 1.0f;
     if (r >= r_cut) return 0.0f;
-    return 0.5f * (1.0f + cospif((r - r_cut + w) / w));
+    // (1 + cos(pi t)) / 2 written as cos^2(pi t / 2): no cancellation where f is small, near r_cut
+    const float c = cospif(0.5f * ((r - r_cut + w) / w));
+    return c * c;
 }
 
 // Position (in floats, 0..3) at which a staged block must start in a 16-byte aligned buffer so that the staged and
@@ -835,6 +837,10 @@ extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int6
     ExpArgs A = make_args(ctx, sys, d_offsets, d_nbr_j, d_rij, d_coeffs);
     const float* pre_D;
     if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, false, &A.pre_G, &pre_D))) return st;
+    if (precision != RASCAL_PS_FP32) {  // the persistent tensor-core kernel where the hypers fit it
+        st = soap_tc(ctx, sys, d_offsets, d_nbr_j, d_rij, A.pre_G, precision, layout, d_coeffs, d_ps);
+        if (st != RASCAL_E_UNSUPPORTED) return st;
+    }
     const int mode = precision == RASCAL_PS_FP32 ? kGramSimt : (precision == RASCAL_PS_BF16 ? kGramBf16 : kGramTf32x3);
     size_t smem;
     int threads;

@@ -94,7 +94,8 @@ __device__ inline void cutoff_and_slope(float r, float r_cut, float w, float& f,
         df = 0.0f;
     } else {
         const float t = (r - r_cut + w) / w;
-        f = 0.5f * (1.0f + cospif(t));
+        const float ch = cospif(0.5f * t);  // (1 + cos(pi t)) / 2 = cos^2(pi t / 2), no cancellation near r_cut
+        f = ch * ch;
         df = -0.5f * 3.14159265358979f / w * sinpif(t);
     }
 }
@@ -563,5 +564,122 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
     const int64_t n3 = 3 * (int64_t)sys->n_atoms;
     k_forces_f64<<<(unsigned)std::min<int64_t>((n3 + 255) / 256, 8192), 256, 0, ctx->stream>>>(n3, f32, d_forces);
     RASCAL_LAUNCH_CHECK("k_forces_f64");
+    return RASCAL_OK;
+}
+
+namespace rascal {
+
+// Per-pair feature gradient, explicitly (a test hook for small cases): for pair p with vector r = r_ji,
+//   d[p][x][n][lm] = d/dr_x [ f_cut(r) I^o_nl(r) Y_lm(r^) ] = (f I)'(r) Y_lm u_x + f I (dY/du - (dY/du . u) u)_x / r,
+// the derivative of the pair's term in c^i_{a_j n l m} (Eq. spherical_expansion_coefficients_gaussians, Appendix B).
+// One CTA per pair: thread m < l_max + 1 runs the m chain of Y and of its polynomial-extension gradient, then the
+// threads cover (n, lm).
+__global__ void k_debug_pair_grad(int64_t P, const float4* __restrict__ rij, const float4* __restrict__ table,
+                                  const float* __restrict__ pre_G, const float* __restrict__ pre_D, int n_max, int l_max,
+                                  int F, int M, float inv_delta, float r_cut, float width, float* __restrict__ out) {
+    extern __shared__ float sdbg[];
+    const int n_lm = (l_max + 1) * (l_max + 1);
+    float4* sY = reinterpret_cast<float4*>(sdbg);  // [n_lm] (Y, dY/dux, dY/duy, dY/duz)
+    float2* sR = reinterpret_cast<float2*>(sY + n_lm);  // [F] (f I, (f I)')
+    const int64_t p = blockIdx.x;
+    const float4 v = rij[p];
+    const float inv_r = v.w > 1e-6f ? 1.0f / v.w : 0.0f;
+    const float x = v.x * inv_r, y = v.y * inv_r, z = v.z * inv_r;
+    const int L1 = l_max + 1;
+    for (int m = threadIdx.x; m < L1; m += blockDim.x) {
+        float cm = 1.0f, sm = 0.0f, cm1 = 0.0f, sm1 = 0.0f;
+        for (int t = 0; t < m; ++t) {
+            cm1 = cm;
+            sm1 = sm;
+            const float nc = cm * x - sm * y;
+            sm = cm * y + sm * x;
+            cm = nc;
+        }
+        const float fm = (float)m;
+        float q2 = 0.0f, q1 = c_ylm_K[m], d2 = 0.0f, d1 = 0.0f;
+        for (int l = m; l < L1; ++l) {
+            float q = q1, dq = d1;
+            if (l > m) {
+                const float Al = c_ylm_A[l * 16 + m], Bl = c_ylm_B[l * 16 + m];
+                q = Al * (z * q1 - Bl * q2);
+                dq = Al * (q1 + z * d1 - Bl * d2);
+                q2 = q1;
+                d2 = d1;
+                q1 = q;
+                d1 = dq;
+            }
+            const int l0 = l * l + l;
+            if (m == 0) {
+                sY[l0] = make_float4(q, 0.0f, 0.0f, dq);
+            } else {
+                sY[l0 + m] = make_float4(q * cm, q * fm * cm1, -q * fm * sm1, dq * cm);
+                sY[l0 - m] = make_float4(q * sm, q * fm * sm1, q * fm * cm1, dq * sm);
+            }
+        }
+    }
+    float f, df;
+    cutoff_and_slope(v.w, r_cut, width, f, df);
+    for (int c = threadIdx.x; c < F; c += blockDim.x) {  // column l n_max + n
+        float g, dg;
+        if (pre_G) {
+            g = pre_G[p * F + c];
+            dg = pre_D[p * F + c];
+        } else {
+            const float xk = v.w * inv_delta;
+            const int k = min(max((int)xk, 0), M - 1);
+            const float u = xk - (float)k;
+            const float4 cf = table[(int64_t)k * F + c];
+            g = fmaf(u, fmaf(u, fmaf(u, cf.w, cf.z), cf.y), cf.x);
+            dg = fmaf(u, fmaf(u, 3.0f * cf.w, 2.0f * cf.z), cf.y) * inv_delta;
+        }
+        sR[c] = make_float2(f * g, df * g + f * dg);
+    }
+    __syncthreads();
+    const int per = n_max * n_lm;
+    float* o = out + p * 3 * per;
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+        const int n = e / n_lm, lm = e - n * n_lm;
+        const int l = (int)sqrtf((float)lm);
+        const float2 R = sR[l * n_max + n];
+        const float4 Yv = sY[lm];
+        const float wu = Yv.y * x + Yv.z * y + Yv.w * z;
+        o[e] = R.y * Yv.x * x + R.x * (Yv.y - wu * x) * inv_r;
+        o[per + e] = R.y * Yv.x * y + R.x * (Yv.z - wu * y) * inv_r;
+        o[2 * per + e] = R.y * Yv.x * z + R.x * (Yv.w - wu * z) * inv_r;
+    }
+}
+
+}  // namespace rascal
+
+extern "C" int rascal_debug_pair_gradients(rascal_ctx* ctx, int64_t n_pairs, const float* d_rij, float* d_dc) {
+    clear_error();
+    if (!ctx) return set_error(RASCAL_E_ARG, "NULL context");
+    if (n_pairs < 0 || n_pairs > (1 << 20)) return set_error(RASCAL_E_ARG, "n_pairs must be in [0, 2^20] (a test hook)");
+    if (n_pairs == 0) return RASCAL_OK;
+    if (!d_rij || !d_dc) return set_error(RASCAL_E_ARG, "NULL device pointer");
+    const float* G = nullptr;
+    const float* D = nullptr;
+    if (ctx->radial != RASCAL_RADIAL_SPLINE) {
+        if (ctx->radial == RASCAL_RADIAL_MLP && !ctx->mlp_params)
+            return set_error(RASCAL_E_ARG, "radial mode MLP needs trained parameters");
+        const size_t words = (size_t)n_pairs * ctx->F;
+        void* base;
+        int st = arena_get(ctx->scratch, carve_bytes(words * 4, words * 4), &base);
+        if (st) return st;
+        Carver cv(base);
+        float* g = cv.take<float>(words);
+        float* d = cv.take<float>(words);
+        const float4* rij = reinterpret_cast<const float4*>(d_rij);
+        st = ctx->radial == RASCAL_RADIAL_MLP ? mlp_infer(ctx, n_pairs, rij, nullptr, g, d)
+                                              : radial_exact_pairs(ctx, n_pairs, rij, g, d);
+        if (st) return st;
+        G = g;
+        D = d;
+    }
+    const size_t smem = sizeof(float4) * ctx->n_lm + sizeof(float2) * ctx->F;
+    k_debug_pair_grad<<<(unsigned)n_pairs, 128, smem, ctx->stream>>>(
+        n_pairs, reinterpret_cast<const float4*>(d_rij), ctx->d_table, G, D, ctx->n_max, ctx->l_max, ctx->F, ctx->M,
+        ctx->inv_delta, (float)ctx->r_cut, (float)ctx->smooth_width, d_dc);
+    RASCAL_LAUNCH_CHECK("k_debug_pair_grad");
     return RASCAL_OK;
 }

@@ -122,3 +122,62 @@ def test_full_size_differentiation_workload_properties(rg):
     assert np.allclose(f.sum(axis=0), 0.0, atol=1e-4 * np.max(np.abs(f)) * np.sqrt(s.n_atoms))
     assert np.allclose(v[0], v[0].T, atol=1e-4 * np.max(np.abs(v)))
     assert abs(np.sum(f * s.positions)) > 0.0
+
+
+def _oracle_pair_terms(d, hyp, derivative):
+    """The oracle's f_cut I^o_nl Y_lm of one pair vector d (and its gradient d/dd_x): [n, lm] or [3, n, lm]."""
+    from oracle import radial as oradial
+    from oracle import ylm as oylm
+
+    r = np.linalg.norm(d, axis=1)
+    f, df = osoap.cutoff(r, hyp["r_cut"], hyp["smooth_width"], derivative=True)
+    I, dI = oradial.integrals(r, hyp["r_cut"], hyp["sigma"], hyp["n_max"], hyp["l_max"], derivative=True)
+    Y, dY = oylm.real_ylm(d, hyp["l_max"], gradient=True)               # [P, lm], [P, lm, 3]
+    lidx = np.array([l for l in range(hyp["l_max"] + 1) for _ in range(2 * l + 1)])
+    R = f[:, None, None] * I[:, :, lidx]                                  # [P, n, lm]
+    if not derivative:
+        return R * Y[:, None, :]
+    dR = df[:, None, None] * I[:, :, lidx] + f[:, None, None] * dI[:, :, lidx]
+    u = d / r[:, None]
+    return (np.einsum("pnk,pk,px->pxnk", dR, Y, u) + np.einsum("pnk,pkx->pxnk", R, dY))
+
+
+def test_debug_pair_gradients_match_oracle(rg):
+    # the per-pair feature gradient written out (Appendix B): d/dr_ji of f_cut I^o_nl Y_lm, against the oracle's
+    # analytic gradient, and the oracle's analytic gradient against its own central differences; pairs of the tiny
+    # workload plus pairs near the cutoff's smooth zone and on the +z / -z axis (the Y_lm pole)
+    import torch
+
+    from synth import config_tiny
+
+    s = config_tiny()
+    hyp = dict(s.hypers)
+    calc = rg.SoapCalculator(**hyp)
+    pl = calc.neighbours(rg.DeviceSystem.from_numpy(s))
+    rij = pl.rij[:300].cpu().numpy().astype(np.float64)
+    extra = np.array([[0.3, -0.2, 4.8], [0.0, 0.0, 2.1], [0.0, 0.0, -3.3], [1e-3, 0.0, 4.0], [4.6, 0.9, -0.5]])
+    d = np.concatenate([rij[:, :3], extra])
+    d32 = d.astype(np.float32)
+    rows = np.concatenate([d32, np.linalg.norm(d32.astype(np.float64), axis=1).astype(np.float32)[:, None]], axis=1)
+    got = calc.debug_pair_gradients(torch.tensor(rows, device="cuda")).cpu().numpy().astype(np.float64)
+    ref = _oracle_pair_terms(d32.astype(np.float64), hyp, True)
+    # the FP32 spline's absolute error enters every pair's block alike: pairs inside the smooth zone of the cutoff
+    # (f_cut = 1) are held to 1e-5 of their own block's maximum; near r_cut, where f_cut and the whole block tend to
+    # zero, the error is held to 1e-5 of the largest pair term of the set instead (the scale that c and the forces see)
+    absd = np.abs(got - ref).reshape(len(d), -1)
+    blk = np.max(np.abs(ref).reshape(len(d), -1), axis=1)
+    r = np.linalg.norm(d32.astype(np.float64), axis=1)
+    inner = r <= hyp["r_cut"] - hyp["smooth_width"]
+    err_in = np.max(absd[inner], axis=1) / blk[inner]
+    err_all = np.max(absd) / np.max(blk)
+    print(f"per-pair gradient: block error {err_in.max():.2e} ({inner.sum()} pairs with f_cut = 1), "
+          f"{err_all:.2e} of the largest term over all {len(d)} pairs")
+    assert err_in.max() <= 1e-5 and err_all <= 1e-5, (err_in.max(), err_all)
+    # the oracle's analytic pair gradient against central differences of its own pair term (h = 1e-5 A)
+    h = 1e-5
+    for x in range(3):
+        e = np.zeros(3)
+        e[x] = h
+        fd = (_oracle_pair_terms(d + e, hyp, False) - _oracle_pair_terms(d - e, hyp, False)) / (2 * h)
+        an = _oracle_pair_terms(d, hyp, True)[:, x]
+        assert np.max(np.abs(fd - an)) <= 1e-7 * max(1.0, np.max(np.abs(an)))

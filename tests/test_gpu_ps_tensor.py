@@ -58,7 +58,10 @@ def _check(rg, s, layouts=("packed", "full"), centres=None):
                 if fused:
                     c2, p = calc.soap(ds, pairs, layout=layout, precision=prec)
                     calc.sync()
-                    assert np.array_equal(c2.cpu().numpy(), c.cpu().numpy())
+                    if prec == "fp32":  # the same pair kernel as rascal_spherical_expansion
+                        assert np.array_equal(c2.cpu().numpy(), c.cpu().numpy())
+                    else:  # the persistent tensor-core kernel has its own pair phase (f_cut folded into Y_lm)
+                        assert block_rel_err(c2.cpu().numpy()[sel], c_ref, 2) <= 1e-5
                     got, r, tol = p.cpu().numpy()[sel], ref, TOL[prec]
                 else:
                     p = calc.power_spectrum(c32_dev, precision=prec, layout=layout)
