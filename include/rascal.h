@@ -133,12 +133,14 @@ int rascal_info(const rascal_ctx* ctx, rascal_info_t* out);
  * label, degenerate geometry, ...) into a status. */
 int rascal_sync(rascal_ctx* ctx);
 
-/* Test hook for the failure path of the tensor-core kernels (no counterpart in the paper): sets the iteration bound
- * of their bounded mbarrier waits (0 restores the built-in bound of 2^22 polls). With a bound of 1 a wait for an MMA
- * batch gives up almost at once: the kernel raises the timeout flag, every role leaves its loop, the MMAs already
- * issued are drained with the built-in bound before the tensor memory is freed, and the next synchronising call
- * returns RASCAL_E_TIMEOUT. The outputs of that call are then incomplete; the context stays usable. */
-int rascal_set_wait_limit(rascal_ctx* ctx, unsigned limit);
+/* Test hook for the failure path of the fused tensor-core Gram (no counterpart in the paper). With polls > 0, the
+ * first MMA-completion wait of every CTA of rascal_soap (precision BF16 or TF32X3) and of the tensor-core forms of
+ * rascal_power_spectrum is made on an mbarrier that nothing arrives at, and gives up after `polls` polls (about
+ * 20 ns apart). The kernel then raises the timeout flag, skips the remaining epilogues, waits (with the built-in
+ * bound of 2^22 polls) for every MMA it issued and frees its tensor memory; the next synchronising call returns
+ * RASCAL_E_TIMEOUT. The outputs of that call are incomplete. polls = 0 switches the hook off; the context stays
+ * usable throughout. Returns RASCAL_E_ARG for a NULL context. */
+int rascal_debug_wait_timeout(rascal_ctx* ctx, unsigned polls);
 
 /* Periodic neighbour list (Appendix B). For every atom i (all structures, in atom order) the pairs (j, n) with
  * |r_j - r_i + n H| < r_cut, (j, n) != (i, 0), sorted by (j, n1, n2, n3). The inclusion test is bit-exact with

@@ -118,7 +118,7 @@ _SIGNATURES = {
     "rascal_gpr_destroy": (None, [C.c_void_p]),
     "rascal_lambda_soap_size": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "rascal_debug_pair_gradients": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
-    "rascal_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint]),
+    "rascal_debug_wait_timeout": (C.c_int, [C.c_void_p, C.c_uint]),
     "rascal_lambda_soap": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p]),
     "rascal_gpr_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),

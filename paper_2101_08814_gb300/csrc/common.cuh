@@ -95,7 +95,6 @@ struct rascal_ctx {
 
     // radial table: FP32 cubic coefficients per interval, [M][F] float4 (c0 + u c1 + u^2 c2 + u^3 c3, u in [0,1])
     float4* d_table;
-    float4* d_table_pad;  // the same with the columns padded to l n_pad + n (zeros for n >= n_max), soap_tc.cu
     int M;
     float inv_delta;  // M / r_cut
     double spline_error, spline_error_fp32;
@@ -109,7 +108,7 @@ struct rascal_ctx {
     int* d_lut;         // [256] label -> species index or -1
 
     unsigned* d_flags;  // device error flags (see kFlag*)
-    unsigned wait_limit;  // iteration bound of the tensor-core kernels' mbarrier waits (0: the built-in bound)
+    unsigned stall_polls;  // test hook: > 0 makes the fused tensor-core Gram's first completion wait run out
     unsigned* h_flags;  // pinned host mirror
 
     rascal::Arena scratch;  // grown on demand, reused across calls
@@ -193,10 +192,6 @@ int power_spectrum_setup(rascal_ctx* ctx);
 // BF16 / TF32x3 power spectrum of given coefficients [n][Q][n_lm] by the fused kernel's tensor-core Gram
 int power_spectrum_tc(rascal_ctx* ctx, int64_t n_centres, const float* d_coeffs, int precision, int layout, float* d_ps);
 int gradients_setup(rascal_ctx* ctx);
-// persistent fused expansion + tensor-core power spectrum (soap_tc.cu); RASCAL_E_UNSUPPORTED if the hypers do not fit
-int soap_tc_setup(rascal_ctx* ctx);
-int soap_tc(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j, const float* d_rij,
-            const float* pre_G, int precision, int layout, float* d_coeffs, float* d_ps);
 // caches the device address of the no-allocation neighbour scratch for ctx->device (neighbours.cu)
 int nbr_static_prepare(rascal_ctx* ctx);
 void lsoap_free(rascal_ctx* ctx);

@@ -435,7 +435,6 @@ extern "C" long long rascal_launch_count(void) { return g_launches.load(std::mem
 extern "C" void rascal_destroy(rascal_ctx* ctx) {
     if (!ctx) return;
     cudaFree(ctx->d_table);
-    cudaFree(ctx->d_table_pad);
     cudaFree(ctx->d_T);
     cudaFree(ctx->d_gto);
     cudaFree(ctx->d_switch);
@@ -549,7 +548,6 @@ static int create_impl(const rascal_hypers* h, void* stream, rascal_ctx** out) {
     ctx->spline_error = errs[0];
     ctx->spline_error_fp32 = errs[1];
     if ((st = expansion_setup(ctx))) return st;
-    if ((st = soap_tc_setup(ctx))) return st;
     if ((st = power_spectrum_setup(ctx))) return st;
     if ((st = gradients_setup(ctx))) return st;
     if ((st = mlp_setup(ctx))) return st;
@@ -605,10 +603,10 @@ extern "C" int rascal_radial_exact_fp64(rascal_ctx* ctx, int64_t n_points, const
     return launch_radial_fp64(ctx, n_points, d_r, d_out, d_dout);
 }
 
-extern "C" int rascal_set_wait_limit(rascal_ctx* ctx, unsigned limit) {
+extern "C" int rascal_debug_wait_timeout(rascal_ctx* ctx, unsigned polls) {
     clear_error();
     if (!ctx) return set_error(RASCAL_E_ARG, "NULL context");
-    ctx->wait_limit = limit;
+    ctx->stall_polls = polls;
     return RASCAL_OK;
 }
 

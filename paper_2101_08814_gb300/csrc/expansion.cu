@@ -33,7 +33,11 @@ namespace rascal {
 
 // kGramSel: the FP32 form restricted to listed features (its own instantiation, so that the full Gram's register
 // allocation is not affected by the selection branch)
-enum GramMode : int { kGramNone = 0, kGramSimt = 1, kGramBf16 = 2, kGramTf32x3 = 3, kGramSel = 4 };
+// kGramRTf32 / kGramRBf16: the tensor-core Gram in rounds of one l (operands staged per round in the pair rows,
+// M = 64 MMAs into two 64-column TMEM slots, epilogue by every warp storing p straight to global memory)
+enum GramMode : int { kGramNone = 0, kGramSimt = 1, kGramBf16 = 2, kGramTf32x3 = 3, kGramSel = 4, kGramRTf32 = 5,
+                      kGramRBf16 = 6 };
+constexpr int kRtcLbo = 144;  // bytes between core matrices adjacent along K (bank groups advance by one per step)
 constexpr int kMaxGroups = kMaxLMax + 2;
 
 struct ExpArgs {
@@ -69,6 +73,11 @@ struct ExpArgs {
     int Qp;                         // SIMT CT row pitch
     int N_mma, tm_cols, slot_cols, lo_off, tiles_bytes;
     int tile_off[kMaxLMax + 1], sbo[kMaxLMax + 1], nk[kMaxLMax + 1];
+    // rounds of one l (kGramRTf32 / kGramRBf16)
+    int rtc_half, rtc_lo, rtc_c_bytes;            // bytes per operand half, offset of the lo tile, staged c bytes
+    int rtc_kq[kMaxLMax + 1];                     // units of four K elements per row (kpad / 4)
+    float rtc_sc[kMaxLMax + 1];                  // operand scale s_l, s_l^2 = k_l
+    uint32_t stall_polls;                        // test hook: > 0 makes the first completion wait run out
 };
 
 __device__ inline float cutoff_fp32(float r, float r_cut, float w) {
@@ -115,9 +124,10 @@ __device__ inline void put_operand(unsigned char* tiles, const ExpArgs& A, int l
 template <int GRAM>
 __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t s_bar[2];
+    __shared__ uint64_t s_bar[4];  // two MMA slots, a drain barrier and one that nothing arrives at (test hook)
     __shared__ uint32_t s_tmem;
     constexpr bool TC = (GRAM == kGramBf16 || GRAM == kGramTf32x3);
+    constexpr bool RTC = (GRAM == kGramRTf32 || GRAM == kGramRBf16);
     const int chunk = A.chunk;
     float4* s_vec = reinterpret_cast<float4*>(smem_raw + A.pair_off);
     float* s_G = reinterpret_cast<float*>(s_vec + chunk);            // [chunk][F_pad]
@@ -145,9 +155,10 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 #pragma unroll 1
                 for (int c = A.Q; c < q_end; ++c) CT[lm * A.Qp + c] = 0.0f;
     }
-    if (TC) {  // K padding and rows >= Q of the operand tiles must read as zero
-        for (int b = tid; b < A.tiles_bytes / 16; b += blockDim.x)
-            reinterpret_cast<uint4*>(gram)[b] = make_uint4(0, 0, 0, 0);
+    if (TC || RTC) {
+        if (TC)  // K padding and rows >= Q of the operand tiles must read as zero
+            for (int b = tid; b < A.tiles_bytes / 16; b += blockDim.x)
+                reinterpret_cast<uint4*>(gram)[b] = make_uint4(0, 0, 0, 0);
         if (warp == 0) {
             tmem_alloc(&s_tmem, (uint32_t)A.tm_cols);
             tmem_relinquish();
@@ -155,6 +166,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         if (tid == 0) {
             mbar_init(&s_bar[0], 1);
             mbar_init(&s_bar[1], 1);
+            mbar_init(&s_bar[2], 1);
+            mbar_init(&s_bar[3], 1);
             fence_mbar_init();
         }
         tc_fence_before();
@@ -181,6 +194,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
     const int g_off = my_l * A.n_pad + 4 * my_nt;   // offset inside a G row
     const int y_off = s_lp[my_l] + 4 * my_mt;       // offset inside a Y row
 
+    float* cdst_r = A.coeffs + (int64_t)i * A.Q * A.n_lm;
+    float* cst_r = stage + stage_shift(cdst_r);
     for (int round = 0; round < (given_c ? 0 : A.rounds); ++round) {
         const int a0 = round * A.S_c;
         const int na = min(A.S_c, A.S - a0);
@@ -328,6 +343,22 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     }
                 }
             }
+            if (RTC) {  // c[q][lm] staged in the (free) pair rows; the operand rounds read it from there
+                const int s_end = 2 * my_l + 1 - 4 * my_mt;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (4 * my_nt + u >= A.n_max) continue;
+                    float* crow = cst_r + (a * A.n_max + 4 * my_nt + u) * A.n_lm + my_l * my_l + 4 * my_mt;
+                    if (s_end >= 4 && (reinterpret_cast<uintptr_t>(crow) & 15) == 0) {
+                        *reinterpret_cast<float4*>(crow) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            if (v < s_end) crow[v] = acc[u][v];
+                    }
+                }
+                continue;
+            }
             if (kCT) {  // tile -> CT[l^2 + s][a n_max + n]; c reaches HBM from CT afterwards
                 float* ct = reinterpret_cast<float*>(gram) + (my_l * my_l + 4 * my_mt) * A.Qp + a * A.n_max + 4 * my_nt;
                 const int v_end = 2 * my_l + 1 - 4 * my_mt, u_end = A.n_max - 4 * my_nt;
@@ -364,6 +395,135 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         }
     }
     if (GRAM == kGramNone) return;
+    if (RTC) {
+        // ---------------------------------------------------------------- tensor-core Gram in rounds of one l
+        fence_proxy_async_smem();
+        __syncthreads();
+        store_staged(cdst_r, cst_r, A.Q * A.n_lm);  // c leaves by one bulk copy (the staged c stays for the operands)
+        const int Q = A.Q, L1n = A.l_max + 1;
+        const bool packed = A.layout == RASCAL_LAYOUT_PACKED;
+        unsigned char* halves = reinterpret_cast<unsigned char*>(stage) + A.rtc_c_bytes;  // behind the staged c
+        const uint32_t halves_s = smem_u32(halves);
+        const uint32_t taddr = s_tmem;
+        const uint32_t idesc = instr_desc(GRAM == kGramRTf32 ? 2u : 1u, 64u, (uint32_t)A.N_mma);
+        float* pout = A.ps + (int64_t)i * A.ps_stride;
+        // operands of l into half h from the staged c: 16-byte units of four K elements (s_l c, zero beyond 2l),
+        // TF32 hi and lo tiles or BF16; every thread takes some of the Q x kpad / 4 units
+        auto write_ops = [&](int l, int h) {
+            unsigned char* base = halves + h * A.rtc_half;
+            const float sl = A.rtc_sc[l];
+            const int n4 = A.rtc_kq[l];
+            const float* cl = cst_r + l * l;
+            for (int e = tid; e < Q * n4; e += blockDim.x) {
+                const int q = e / n4, k4 = e - q * n4;
+                const float* src = cl + q * A.n_lm + 4 * k4;
+                const int s0 = 4 * k4;
+                const float x0 = s0 <= 2 * l ? sl * src[0] : 0.0f;
+                const float x1 = s0 + 1 <= 2 * l ? sl * src[1] : 0.0f;
+                const float x2 = s0 + 2 <= 2 * l ? sl * src[2] : 0.0f;
+                const float x3 = s0 + 3 <= 2 * l ? sl * src[3] : 0.0f;
+                const int row = (q >> 3) * A.sbo[l] + (q & 7) * 16;
+                if (GRAM == kGramRTf32) {
+                    const float h0 = __uint_as_float(__float_as_uint(x0) & 0xFFFFE000u);
+                    const float h1 = __uint_as_float(__float_as_uint(x1) & 0xFFFFE000u);
+                    const float h2 = __uint_as_float(__float_as_uint(x2) & 0xFFFFE000u);
+                    const float h3 = __uint_as_float(__float_as_uint(x3) & 0xFFFFE000u);
+                    const int off = row + k4 * kRtcLbo;
+                    *reinterpret_cast<float4*>(base + off) = make_float4(h0, h1, h2, h3);
+                    *reinterpret_cast<float4*>(base + A.rtc_lo + off) = make_float4(x0 - h0, x1 - h1, x2 - h2, x3 - h3);
+                } else {
+                    const int off = row + (k4 >> 1) * kRtcLbo + (k4 & 1) * 8;
+                    const __nv_bfloat162 b01 = __floats2bfloat162_rn(x0, x1), b23 = __floats2bfloat162_rn(x2, x3);
+                    uint2 w;
+                    w.x = *reinterpret_cast<const uint32_t*>(&b01);
+                    w.y = *reinterpret_cast<const uint32_t*>(&b23);
+                    *reinterpret_cast<uint2*>(base + off) = w;
+                }
+            }
+        };
+        auto issue = [&](int l, int sl) {
+            const uint32_t d = taddr + (uint32_t)(sl * A.slot_cols);
+            const uint32_t a0 = halves_s + (uint32_t)(sl * A.rtc_half);
+            for (int kk = 0; kk < A.nk[l]; ++kk) {
+                const uint32_t a_addr = a0 + (uint32_t)(kk * 2 * kRtcLbo);
+                const uint64_t da = smem_desc(a_addr, kRtcLbo, (uint32_t)A.sbo[l]);
+                if (GRAM == kGramRTf32) {
+                    const uint64_t dl = smem_desc(a_addr + (uint32_t)A.rtc_lo, kRtcLbo, (uint32_t)A.sbo[l]);
+                    mma_tf32_ss(d, da, da, idesc, kk > 0);
+                    mma_tf32_ss(d, da, dl, idesc, 1);
+                    mma_tf32_ss(d, dl, da, idesc, 1);
+                } else {
+                    mma_bf16_ss(d, da, da, idesc, kk > 0);
+                }
+            }
+            mma_commit(&s_bar[sl]);
+        };
+        // rows of this warp (M = 64: TMEM lanes 32 quad + 0..15 hold rows 16 quad + 0..15); the warps of a quadrant
+        // share its 16-column chunks
+        const int quad = warp & 3, wq = warp >> 2, nwq = (nwarps - quad + 3) >> 2;
+        const int r = 16 * quad + lane;
+        const bool row_ok = lane < 16 && r < Q;
+        const int cend = packed ? min(Q - 1, 16 * quad + 15) + 1 : Q;
+        __shared__ int s_fail;
+        if (tid == 0) s_fail = 0;
+        // round k handles l = l_max - k in slot / operand half k & 1; the MMAs of round k + 1 are issued before
+        // the epilogue of round k
+        write_ops(A.l_max, 0);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) issue(A.l_max, 0);
+        for (int k = 0; k < L1n; ++k) {
+            const int l = A.l_max - k, sl = k & 1;
+            if (k + 1 < L1n) write_ops(l - 1, sl ^ 1);  // its half was read by round k - 1's MMAs, waited for below
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();  // operands of round k + 1 written; round k - 1's epilogue done with slot sl ^ 1
+            tc_fence_after();
+            const bool go = s_fail == 0;
+            if (tid == 0 && k + 1 < L1n && go) issue(l - 1, sl ^ 1);
+            // the test hook points the first wait at a barrier that no MMA signals, bounded by stall_polls polls
+            const bool stall = A.stall_polls != 0 && k == 0;
+            const bool done = go && __all_sync(0xffffffffu, mbar_wait_bounded(stall ? &s_bar[3] : &s_bar[sl],
+                                                                              (uint32_t)((k >> 1) & 1),
+                                                                              stall ? A.stall_polls : (1u << 22)));
+            if (!done) {
+                if (lane == 0) s_fail = 1;
+                continue;
+            }
+            tc_fence_after();
+            if (16 * quad < Q) {
+                const uint32_t tl = taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)(sl * A.slot_cols);
+                float* out = pout + (int64_t)l * A.per_l;
+                for (int c0 = 16 * wq; c0 < cend; c0 += 16 * nwq) {
+                    float v[16];
+                    tmem_ld16(tl + (uint32_t)c0, v);
+                    // packed (q1, q2) = (column c, row r), c <= r, at c (2Q - c - 1) / 2 + r; FULL: at c Q + r
+                    int o = packed ? c0 * (2 * Q - c0 - 1) / 2 + r : c0 * Q + r;
+                    const int dd = row_ok ? (packed ? r - c0 : Q - 1 - c0) : -1;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (j <= dd) out[o] = v[j];
+                        o += packed ? Q - 1 - (c0 + j) : Q;
+                    }
+                }
+            }
+        }
+        if (tid == 0) {  // every MMA issued above has completed before the tensor memory is freed
+            if (s_fail) atomicOr(A.flags, kFlagTimeout);
+            mma_commit(&s_bar[2]);
+            if (!mbar_wait_bounded(&s_bar[2], 0u)) atomicOr(A.flags, kFlagTimeout);
+        }
+        if (tid == 0) bulk_wait_all();
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tc_fence_after();
+            tmem_dealloc(s_tmem, (uint32_t)A.tm_cols);
+        }
+        return;
+    }
     if (given_c) {  // operand tiles from the given coefficients of this centre
         const float* cc = A.c_in + (int64_t)i * A.Q * A.n_lm;
         for (int e = tid; e < A.Q * A.n_lm; e += blockDim.x) {
@@ -486,8 +646,12 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
             const int lo = A.g_lo[gi];
             float* dst = pout + (int64_t)lo * A.per_l;
             float* st = stage + (gi & 1) * A.p_half + stage_shift(dst);
-            // warp-uniform, since tcgen05.ld is issued by whole warps
-            const bool done = __all_sync(0xffffffffu, mbar_wait_bounded(&s_bar[l & 1], (uint32_t)((l >> 1) & 1)));
+            // warp-uniform, since tcgen05.ld is issued by whole warps; the test hook points the first wait at a
+            // barrier that no MMA signals
+            const bool stall = A.stall_polls != 0 && l == 0;
+            const bool done = __all_sync(0xffffffffu, mbar_wait_bounded(stall ? &s_bar[3] : &s_bar[l & 1],
+                                                                        (uint32_t)((l >> 1) & 1),
+                                                                        stall ? A.stall_polls : (1u << 22)));
             tc_fence_after();
             if (done && 32 * quad < A.Q) {
                 const float kl = A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f;
@@ -522,9 +686,10 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 }
             }
         }
-        if (!ok) {  // an MMA batch did not complete in time: flag it and give the outstanding ones another bound
-            if (tid == 0) atomicOr(A.flags, kFlagTimeout);
-            for (int sl = 0; sl < 2; ++sl) mbar_wait_bounded(&s_bar[sl], 0u);
+        if (!ok && tid == 0) {  // a wait ran out: flag it, then wait (bounded) for every MMA this thread issued
+            atomicOr(A.flags, kFlagTimeout);
+            mma_commit(&s_bar[2]);
+            if (!mbar_wait_bounded(&s_bar[2], 0u)) atomicOr(A.flags, kFlagTimeout);
         }
         if (tid == 0) bulk_wait_all();
         tc_fence_before();
@@ -592,7 +757,7 @@ int expansion_setup(rascal_ctx* ctx) {
     int st;
     if ((st = set_attr<kGramNone>()) || (st = set_attr<kGramSimt>()) || (st = set_attr<kGramSel>()) ||
         (st = set_attr<kGramBf16>()) ||
-        (st = set_attr<kGramTf32x3>()))
+        (st = set_attr<kGramTf32x3>()) || (st = set_attr<kGramRTf32>()) || (st = set_attr<kGramRBf16>()))
         return st;
     RASCAL_CUDA(cudaStreamSynchronize(ctx->stream));
     return RASCAL_OK;
@@ -645,6 +810,7 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
     A.ps = d_ps;
     A.layout = layout;
     A.ps_norm = ctx->ps_norm;
+    A.stall_polls = ctx->stall_polls;
     A.Q = Q;
     A.per_l = layout == RASCAL_LAYOUT_PACKED ? Q * (Q + 1) / 2 : Q * Q;
     A.ps_stride = (int64_t)(ctx->l_max + 1) * A.per_l;
@@ -654,6 +820,35 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
     size_t gram_bytes = 0;
     size_t stage_need = 0;
     size_t tail_end = 0;  // tensor cores: end of the bytes the last MMA reads
+    if (mode == kGramRTf32 || mode == kGramRBf16) {
+        // one species round, M = 64 rows, N <= 64 columns per TMEM slot; one l per round
+        if (P.rounds != 1 || Q > 64) return RASCAL_E_UNSUPPORTED;
+        const bool tf32 = mode == kGramRTf32;
+        const int esz = tf32 ? 4 : 2, kstep = tf32 ? 8 : 16, e16 = 16 / esz;
+        A.N_mma = std::max(8, (Q + 7) / 8 * 8);
+        int sbo_max = 0;
+        for (int l = 0; l < L1; ++l) {
+            const int kpad = (2 * l + 1 + kstep - 1) / kstep * kstep;
+            A.nk[l] = kpad / kstep;
+            A.rtc_kq[l] = kpad / 4;
+            A.sbo[l] = (kpad / e16) * kRtcLbo;
+            sbo_max = std::max(sbo_max, A.sbo[l]);
+            A.rtc_sc[l] = ctx->ps_norm ? (float)std::pow(2.0 * l + 1.0, -0.25) : 1.0f;
+        }
+        A.rtc_lo = 8 * sbo_max;  // an M = 64 MMA reads 8 groups of 8 rows
+        A.rtc_half = tf32 ? 2 * A.rtc_lo : A.rtc_lo;
+        A.slot_cols = 64;
+        A.tm_cols = 128;
+        A.pair_off = 0;
+        A.rtc_c_bytes = (int)align_up(sizeof(float) * ((size_t)Q * ctx->n_lm + 3), 16);
+        const size_t need = (size_t)A.rtc_c_bytes + 2 * (size_t)A.rtc_half;
+        size_t exp_bytes = P.smem;
+        if (need > pair_region * sizeof(float)) exp_bytes += need - pair_region * sizeof(float);
+        A.gram_off = (int)align_up(exp_bytes, 1024);
+        *smem = exp_bytes;
+        *threads = std::max(P.threads, 128);
+        return *smem > 200 * 1024 ? RASCAL_E_UNSUPPORTED : RASCAL_OK;
+    }
     if (mode == kGramSimt) {
         // row pitch: a multiple of 4 floats with Qp / 4 odd, so float4 reads down a column of CT are conflict-free
         A.Qp = ((Q + 3) / 4 | 1) * 4;
@@ -837,9 +1032,14 @@ extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int6
     ExpArgs A = make_args(ctx, sys, d_offsets, d_nbr_j, d_rij, d_coeffs);
     const float* pre_D;
     if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, false, &A.pre_G, &pre_D))) return st;
-    if (precision != RASCAL_PS_FP32) {  // the persistent tensor-core kernel where the hypers fit it
-        st = soap_tc(ctx, sys, d_offsets, d_nbr_j, d_rij, A.pre_G, precision, layout, d_coeffs, d_ps);
+    if (precision == RASCAL_PS_TF32X3) {  // TF32x3: the tensor-core Gram in rounds of one l where the hypers fit it
+        ExpArgs R = A;
+        size_t smem_r;
+        int threads_r;
+        st = make_gram(ctx, kGramRTf32, layout, d_ps, R, &smem_r, &threads_r);
+        if (st == RASCAL_OK) return launch_expansion<kGramRTf32>(ctx, R, sys->n_atoms, threads_r, smem_r);
         if (st != RASCAL_E_UNSUPPORTED) return st;
+        clear_error();
     }
     const int mode = precision == RASCAL_PS_FP32 ? kGramSimt : (precision == RASCAL_PS_BF16 ? kGramBf16 : kGramTf32x3);
     size_t smem;

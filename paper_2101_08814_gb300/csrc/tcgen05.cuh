@@ -55,10 +55,23 @@ __device__ inline bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint3
         : "memory");
     return ok != 0;
 }
-// bounded wait; returns false on timeout
+// non-blocking test of the phase (no suspension)
+__device__ inline bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; returns false on timeout. Polls with the non-blocking test and a short sleep between polls, so that
+// the bound counts polls (a single poll when max_iter is 1) and a waiting warp takes few issue slots.
 __device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t max_iter = (1u << 22)) {
-    for (uint32_t it = 0; it < max_iter; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
+    for (uint32_t it = 0; it < max_iter; ++it) {
+        if (mbar_test_wait(bar, parity)) return true;
+        __nanosleep(20);
+    }
     return false;
 }
 
