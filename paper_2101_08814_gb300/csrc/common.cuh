@@ -67,6 +67,36 @@ struct Arena {
 //   S_c species accumulated concurrently, rounds = ceil(n_species / S_c)
 struct LsoapTable;  // lambda-SOAP coupling tables (lambda_soap.cu)
 
+// Hyper shapes with their own compiled instances of the fused FP32 kernel (expansion.cu) and the gradient kernel
+// (gradients.cu): the batch, large and diff workloads' n_max, l_max and species count. Index 0 stands for the
+// runtime-shaped kernels, which serve every other shape. The derived sizes below mirror the host plan (make_plan,
+// make_gram); the host launches a shaped instance only when every one of them equals the plan's value.
+struct ExpShape {
+    int n_max, l_max, S;
+};
+constexpr ExpShape kExpShapes[] = {{0, 0, 0}, {12, 9, 4}, {10, 8, 3}, {8, 6, 2}};
+constexpr int kNumExpShapes = sizeof(kExpShapes) / sizeof(kExpShapes[0]);
+constexpr int exp_npad(int n_max) { return (n_max + 3) / 4 * 4; }
+// Y row offset of l: sum over l' < l of ceil4(2l' + 1), i.e. 4 k (k + 1) for l = 2k and 4 (k + 1)^2 for l = 2k + 1
+constexpr int exp_lp(int l) { return (l & 1) ? 4 * ((l >> 1) + 1) * ((l >> 1) + 1) : 4 * (l >> 1) * ((l >> 1) + 1); }
+constexpr int exp_ly(int l_max) { return (exp_lp(l_max + 1) / 4 | 1) * 4; }
+constexpr int exp_qp(int Q) { return ((Q + 3) / 4 | 1) * 4; }
+constexpr int exp_ts(int n_max, int l_max) { return exp_npad(n_max) / 4 * (exp_lp(l_max + 1) / 4); }
+constexpr int exp_sc(int n_max, int l_max, int S) {
+    const int w = (exp_ts(n_max, l_max) + 31) / 32;
+    return w > 16 ? 1 : (16 / w < S ? (16 / w < 1 ? 1 : 16 / w) : S);
+}
+constexpr size_t exp_pair_smem(int n_max, int l_max, int chunk) {
+    const int fpad = (l_max + 1) * exp_npad(n_max);
+    return (size_t)chunk * 16 + (size_t)chunk * (fpad + exp_ly(l_max)) * 4 + (size_t)chunk * 12 +
+           (size_t)(kMaxSpecies + 1 + kMaxLMax + 2 + fpad) * 4 + 64;
+}
+constexpr int exp_chunk(int n_max, int l_max) {
+    int chunk = 32;  // about 30 KB for n_max 12, l_max 9: four CTAs per SM
+    while (chunk > 8 && exp_pair_smem(n_max, l_max, chunk) > 56 * 1024) chunk /= 2;
+    return chunk;
+}
+
 struct ExpPlan {
     int n_pad, F_pad, Lp;
     int Ly;           // Y row pitch in the expansion kernel: Lp rounded up so that Ly / 4 is odd (conflict-free rows)

@@ -121,39 +121,49 @@ __device__ inline void put_operand(unsigned char* tiles, const ExpArgs& A, int l
     }
 }
 
-template <int GRAM>
+template <int GRAM, int SHAPE = 0>
 __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
+    // hyper shape: compile-time constants for the instantiated shapes (the index arithmetic folds, loops of known
+    // length unroll), the launch arguments otherwise
+    constexpr ExpShape C = kExpShapes[SHAPE];
+    const int kNmax = SHAPE ? C.n_max : A.n_max, kLmax = SHAPE ? C.l_max : A.l_max, kS = SHAPE ? C.S : A.S;
+    const int kQ = SHAPE ? C.n_max * C.S : A.Q, kNlm = SHAPE ? (C.l_max + 1) * (C.l_max + 1) : A.n_lm;
+    const int kNpad = SHAPE ? exp_npad(C.n_max) : A.n_pad, kFpad = SHAPE ? (C.l_max + 1) * exp_npad(C.n_max) : A.F_pad;
+    const int kF = SHAPE ? (C.l_max + 1) * C.n_max : A.F, kLy = SHAPE ? exp_ly(C.l_max) : A.Ly;
+    const int kQp = SHAPE ? exp_qp(C.n_max * C.S) : A.Qp, kTs = SHAPE ? exp_ts(C.n_max, C.l_max) : A.T_s;
+    const int kWs = SHAPE ? (exp_ts(C.n_max, C.l_max) + 31) / 32 : A.W_s;
+    const int kSc = SHAPE ? exp_sc(C.n_max, C.l_max, C.S) : A.S_c;
+    const int kRounds = SHAPE ? (C.S + exp_sc(C.n_max, C.l_max, C.S) - 1) / exp_sc(C.n_max, C.l_max, C.S) : A.rounds;
+    const int kChunk = SHAPE ? exp_chunk(C.n_max, C.l_max) : A.chunk;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t s_bar[4];  // two MMA slots, a drain barrier and one that nothing arrives at (test hook)
     __shared__ uint32_t s_tmem;
     constexpr bool TC = (GRAM == kGramBf16 || GRAM == kGramTf32x3);
     constexpr bool RTC = (GRAM == kGramRTf32 || GRAM == kGramRBf16);
-    const int chunk = A.chunk;
+    const int chunk = kChunk;
     float4* s_vec = reinterpret_cast<float4*>(smem_raw + A.pair_off);
     float* s_G = reinterpret_cast<float*>(s_vec + chunk);            // [chunk][F_pad]
-    float* s_Y = s_G + (size_t)chunk * A.F_pad;                       // [chunk][Ly]
-    float* s_fc = s_Y + (size_t)chunk * A.Ly;
+    float* s_Y = s_G + (size_t)chunk * kFpad;                       // [chunk][Ly]
+    float* s_fc = s_Y + (size_t)chunk * kLy;
     int* s_spc = reinterpret_cast<int*>(s_fc + chunk);
     int* s_list = s_spc + chunk;
     int* s_start = s_list + chunk;                                    // [kMaxSpecies + 1]
-    int* s_lp = s_start + (kMaxSpecies + 1);                          // [kMaxLMax + 2]
-    int* s_fmap = s_lp + (kMaxLMax + 2);                              // [F_pad]
+    int* s_fmap = s_start + (kMaxSpecies + 1) + (kMaxLMax + 2);        // [F_pad]
     unsigned char* gram = smem_raw + A.gram_off;                      // CT or tiles
     float* stage = s_G;                                               // reused once the pairs are done
 
     const int i = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    if (tid < kMaxLMax + 2) s_lp[tid] = A.lp[tid];
     #pragma unroll 1
-    for (int t = tid; t < A.F_pad; t += blockDim.x) s_fmap[t] = A.fmap[t];
+    for (int t = tid; t < kFpad; t += blockDim.x) s_fmap[t] = A.fmap[t];
     constexpr bool kCT = (GRAM == kGramSimt || GRAM == kGramSel);  // c held transposed in shared memory
     if (kCT) {  // columns Q..ceil4(Q)-1 of CT are read by the edge tiles and must be zero
         float* CT = reinterpret_cast<float*>(gram);
-        const int q_end = (A.Q + 3) & ~3;
-        if (q_end > A.Q)
-            for (int lm = tid; lm < A.n_lm; lm += blockDim.x)
+        const int q_end = (kQ + 3) & ~3;
+        if (q_end > kQ)
+            for (int lm = tid; lm < kNlm; lm += blockDim.x)
                 #pragma unroll 1
-                for (int c = A.Q; c < q_end; ++c) CT[lm * A.Qp + c] = 0.0f;
+                for (int c = kQ; c < q_end; ++c) CT[lm * kQp + c] = 0.0f;
     }
     if (TC || RTC) {
         if (TC)  // K padding and rows >= Q of the operand tiles must read as zero
@@ -177,29 +187,29 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
     const int seg_len = given_c ? 0 : (int)(A.offsets[i + 1] - seg_beg);
     const float4* seg_rij = A.rij + seg_beg;
     const int* seg_j = A.nbr_j + seg_beg;
-    const float* seg_G = A.pre_G ? A.pre_G + seg_beg * A.F : nullptr;
-    const int L1 = A.l_max + 1;
+    const float* seg_G = A.pre_G ? A.pre_G + seg_beg * kF : nullptr;
+    const int L1 = kLmax + 1;
 
     int my_l = 0, my_nt = 0, my_mt = 0;
-    const int group_threads = 32 * A.W_s;
+    const int group_threads = 32 * kWs;
     const int g = tid / group_threads;
     const int task = tid - g * group_threads;
-    if (task < A.T_s) {
+    if (task < kTs) {
         const int packed = A.tasks[task];
         my_l = packed & 0xff;
         my_nt = (packed >> 8) & 0xff;
         my_mt = (packed >> 16) & 0xff;
     }
     __syncthreads();
-    const int g_off = my_l * A.n_pad + 4 * my_nt;   // offset inside a G row
-    const int y_off = s_lp[my_l] + 4 * my_mt;       // offset inside a Y row
+    const int g_off = my_l * kNpad + 4 * my_nt;   // offset inside a G row
+    const int y_off = exp_lp(my_l) + 4 * my_mt;       // offset inside a Y row
 
-    float* cdst_r = A.coeffs + (int64_t)i * A.Q * A.n_lm;
+    float* cdst_r = A.coeffs + (int64_t)i * kQ * kNlm;
     float* cst_r = stage + stage_shift(cdst_r);
-    for (int round = 0; round < (given_c ? 0 : A.rounds); ++round) {
-        const int a0 = round * A.S_c;
-        const int na = min(A.S_c, A.S - a0);
-        const bool active = (g < na) && (task < A.T_s);
+    for (int round = 0; round < (given_c ? 0 : kRounds); ++round) {
+        const int a0 = round * kSc;
+        const int na = min(kSc, kS - a0);
+        const bool active = (g < na) && (task < kTs);
         uint64_t ap[4][2];  // the thread's 4 x 4 tile as (v, v+1) pairs of FP32 sums
 #pragma unroll
         for (int u = 0; u < 4; ++u) ap[u][0] = ap[u][1] = 0ull;
@@ -255,24 +265,24 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                         sm = cm * y + sm * x;
                         cm = nc2;
                     }
-                    float* yrow = s_Y + q * A.Ly;
+                    float* yrow = s_Y + q * kLy;
                     float q2 = 0.0f, q1 = km;
                     if (m == 0) {
-                        yrow[s_lp[0]] = q1;
+                        yrow[exp_lp(0)] = q1;
                         #pragma unroll 1
                         for (int l = 1; l < L1; ++l) {
                             const float qq = c_ylm_A[l * 16] * (z * q1 - c_ylm_B[l * 16] * q2);
-                            yrow[s_lp[l] + l] = qq;
+                            yrow[exp_lp(l) + l] = qq;
                             q2 = q1;
                             q1 = qq;
                         }
                     } else {
-                        yrow[s_lp[m] + 2 * m] = q1 * cm;
-                        yrow[s_lp[m]] = q1 * sm;
+                        yrow[exp_lp(m) + 2 * m] = q1 * cm;
+                        yrow[exp_lp(m)] = q1 * sm;
                         #pragma unroll 1
                         for (int l = m + 1; l < L1; ++l) {
                             const float qq = c_ylm_A[l * 16 + m] * (z * q1 - c_ylm_B[l * 16 + m] * q2);
-                            float* yl = yrow + s_lp[l] + l;
+                            float* yl = yrow + exp_lp(l) + l;
                             yl[m] = qq * cm;
                             yl[-m] = qq * sm;
                             q2 = q1;
@@ -286,10 +296,10 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
             for (int q = nwarps - 1 - warp; q < n_list; q += nwarps) {
                 const int p = s_list[q];
                 const float fc = s_fc[p];
-                float* grow = s_G + q * A.F_pad;
+                float* grow = s_G + q * kFpad;
                 if (A.pre_G) {  // per-pair values (EXACT / MLP radial modes)
-                    const float* prow = seg_G + (pos + p) * A.F;
-                    for (int fp = lane; fp < A.F_pad; fp += 32) {
+                    const float* prow = seg_G + (pos + p) * kF;
+                    for (int fp = lane; fp < kFpad; fp += 32) {
                         const int col = s_fmap[fp];
                         grow[fp] = col >= 0 ? fc * __ldg(prow + col) : 0.0f;
                     }
@@ -297,8 +307,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     const float x = s_vec[p].w * A.inv_delta;
                     const int k = min(max((int)x, 0), A.M - 1);
                     const float u = x - (float)k;
-                    const float4* trow = A.table + k * A.F;
-                    for (int fp = lane; fp < A.F_pad; fp += 32) {
+                    const float4* trow = A.table + k * kF;
+                    for (int fp = lane; fp < kFpad; fp += 32) {
                         const int col = s_fmap[fp];
                         const float4 c = col >= 0 ? __ldg(trow + col) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                         grow[fp] = fc * fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
@@ -309,8 +319,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
             if (active) {
                 const int beg = s_start[g], end = s_start[g + 1];
                 for (int q = beg; q < end; ++q) {
-                    const float4 gv = *reinterpret_cast<const float4*>(s_G + q * A.F_pad + g_off);
-                    const float4 yv = *reinterpret_cast<const float4*>(s_Y + q * A.Ly + y_off);
+                    const float4 gv = *reinterpret_cast<const float4*>(s_G + q * kFpad + g_off);
+                    const float4 yv = *reinterpret_cast<const float4*>(s_Y + q * kLy + y_off);
                     const uint64_t y01 = f2_pack(yv.x, yv.y), y23 = f2_pack(yv.z, yv.w);
                     const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
 #pragma unroll
@@ -339,7 +349,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int n = 4 * my_nt + u;
-                        if (n < A.n_max) acc[u][0] += fc0 * A.table[n].x * c_ylm_K[0];
+                        if (n < kNmax) acc[u][0] += fc0 * A.table[n].x * c_ylm_K[0];
                     }
                 }
             }
@@ -347,8 +357,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 const int s_end = 2 * my_l + 1 - 4 * my_mt;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    if (4 * my_nt + u >= A.n_max) continue;
-                    float* crow = cst_r + (a * A.n_max + 4 * my_nt + u) * A.n_lm + my_l * my_l + 4 * my_mt;
+                    if (4 * my_nt + u >= kNmax) continue;
+                    float* crow = cst_r + (a * kNmax + 4 * my_nt + u) * kNlm + my_l * my_l + 4 * my_mt;
                     if (s_end >= 4 && (reinterpret_cast<uintptr_t>(crow) & 15) == 0) {
                         *reinterpret_cast<float4*>(crow) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
                     } else {
@@ -360,13 +370,13 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 continue;
             }
             if (kCT) {  // tile -> CT[l^2 + s][a n_max + n]; c reaches HBM from CT afterwards
-                float* ct = reinterpret_cast<float*>(gram) + (my_l * my_l + 4 * my_mt) * A.Qp + a * A.n_max + 4 * my_nt;
-                const int v_end = 2 * my_l + 1 - 4 * my_mt, u_end = A.n_max - 4 * my_nt;
-                const bool vec = u_end >= 4 && (A.n_max & 3) == 0;
+                float* ct = reinterpret_cast<float*>(gram) + (my_l * my_l + 4 * my_mt) * kQp + a * kNmax + 4 * my_nt;
+                const int v_end = 2 * my_l + 1 - 4 * my_mt, u_end = kNmax - 4 * my_nt;
+                const bool vec = u_end >= 4 && (kNmax & 3) == 0;
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     if (v >= v_end) break;
-                    float* row = ct + v * A.Qp;
+                    float* row = ct + v * kQp;
                     if (vec) {
                         *reinterpret_cast<float4*>(row) = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
                     } else {
@@ -377,18 +387,18 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 }
                 continue;
             }
-            float* out = A.coeffs + ((int64_t)i * A.S + a) * A.n_max * A.n_lm + my_l * my_l;
+            float* out = A.coeffs + ((int64_t)i * kS + a) * kNmax * kNlm + my_l * my_l;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int n = 4 * my_nt + u;
-                if (n >= A.n_max) continue;
-                const int q = a * A.n_max + n;
+                if (n >= kNmax) continue;
+                const int q = a * kNmax + n;
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     const int s = 4 * my_mt + v;
                     if (s > 2 * my_l) continue;
                     const float cv = acc[u][v];
-                    out[n * A.n_lm + s] = cv;
+                    out[n * kNlm + s] = cv;
                     if (TC) put_operand<GRAM>(gram, A, my_l, q, s, cv);
                 }
             }
@@ -399,8 +409,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         // ---------------------------------------------------------------- tensor-core Gram in rounds of one l
         fence_proxy_async_smem();
         __syncthreads();
-        store_staged(cdst_r, cst_r, A.Q * A.n_lm);  // c leaves by one bulk copy (the staged c stays for the operands)
-        const int Q = A.Q, L1n = A.l_max + 1;
+        store_staged(cdst_r, cst_r, kQ * kNlm);  // c leaves by one bulk copy (the staged c stays for the operands)
+        const int Q = kQ, L1n = kLmax + 1;
         const bool packed = A.layout == RASCAL_LAYOUT_PACKED;
         unsigned char* halves = reinterpret_cast<unsigned char*>(stage) + A.rtc_c_bytes;  // behind the staged c
         const uint32_t halves_s = smem_u32(halves);
@@ -416,7 +426,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
             const float* cl = cst_r + l * l;
             for (int e = tid; e < Q * n4; e += blockDim.x) {
                 const int q = e / n4, k4 = e - q * n4;
-                const float* src = cl + q * A.n_lm + 4 * k4;
+                const float* src = cl + q * kNlm + 4 * k4;
                 const int s0 = 4 * k4;
                 const float x0 = s0 <= 2 * l ? sl * src[0] : 0.0f;
                 const float x1 = s0 + 1 <= 2 * l ? sl * src[1] : 0.0f;
@@ -468,14 +478,14 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         if (tid == 0) s_fail = 0;
         // round k handles l = l_max - k in slot / operand half k & 1; the MMAs of round k + 1 are issued before
         // the epilogue of round k
-        write_ops(A.l_max, 0);
+        write_ops(kLmax, 0);
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (tid == 0) issue(A.l_max, 0);
+        if (tid == 0) issue(kLmax, 0);
         for (int k = 0; k < L1n; ++k) {
-            const int l = A.l_max - k, sl = k & 1;
+            const int l = kLmax - k, sl = k & 1;
             if (k + 1 < L1n) write_ops(l - 1, sl ^ 1);  // its half was read by round k - 1's MMAs, waited for below
             fence_proxy_async_smem();
             tc_fence_before();
@@ -525,9 +535,9 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         return;
     }
     if (given_c) {  // operand tiles from the given coefficients of this centre
-        const float* cc = A.c_in + (int64_t)i * A.Q * A.n_lm;
-        for (int e = tid; e < A.Q * A.n_lm; e += blockDim.x) {
-            const int q = e / A.n_lm, lm = e - q * A.n_lm;
+        const float* cc = A.c_in + (int64_t)i * kQ * kNlm;
+        for (int e = tid; e < kQ * kNlm; e += blockDim.x) {
+            const int q = e / kNlm, lm = e - q * kNlm;
             const int l = (int)sqrtf((float)lm);
             put_operand<GRAM>(gram, A, l, q, lm - l * l, __ldg(cc + e));
         }
@@ -540,10 +550,10 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         __syncthreads();
         const float* CT = reinterpret_cast<const float*>(gram);
         {   // c[q][lm] = CT[lm][q]: lanes over lm (coalesced stores), float4 reads along q
-            float* cdst = A.coeffs + (int64_t)i * A.Q * A.n_lm;
-            const int n_lm = A.n_lm, Qp = A.Qp;
-            for (int q = 4 * warp; q < A.Q; q += 4 * nwarps) {
-                const int nq = A.Q - q;
+            float* cdst = A.coeffs + (int64_t)i * kQ * kNlm;
+            const int n_lm = kNlm, Qp = kQp;
+            for (int q = 4 * warp; q < kQ; q += 4 * nwarps) {
+                const int nq = kQ - q;
                 float* d = cdst + q * n_lm + lane;
                 const float* src = CT + lane * Qp + q;
 #pragma unroll 1
@@ -562,9 +572,9 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 const int packed = __ldg(A.sel + k);
                 const int l = packed & 0xff, q1 = (packed >> 8) & 0xff, q2 = (packed >> 16) & 0xff;
                 float acc = 0.0f;
-                if (l <= A.l_max) {
-                    const float* r = CT + l * l * A.Qp;
-                    for (int m = 0; m <= 2 * l; ++m, r += A.Qp) acc = fmaf(r[q1], r[q2], acc);
+                if (l <= kLmax) {
+                    const float* r = CT + l * l * kQp;
+                    for (int m = 0; m <= 2 * l; ++m, r += kQp) acc = fmaf(r[q1], r[q2], acc);
                     if (A.ps_norm) acc *= rsqrtf((float)(2 * l + 1));
                 }
                 po[k] = acc;
@@ -590,8 +600,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 const int packed = __ldg(&A.ps_tasks[t]);
                 const int l = packed & 0xff, t1 = (packed >> 8) & 0xff, t2 = (packed >> 16) & 0xff;
                 float acc[4][4];
-                gram_tile_fp32(CT, A.Qp, l, t1, t2, acc);
-                store_tile_fp32(st + (l - lo) * A.per_l, A.Q, A.layout, t1, t2,
+                gram_tile_fp32(CT, kQp, l, t1, t2, acc);
+                store_tile_fp32(st + (l - lo) * A.per_l, kQ, A.layout, t1, t2,
                                 A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f, acc);
             }
             fence_proxy_async_smem();
@@ -614,7 +624,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         const uint32_t taddr = s_tmem;
         const uint32_t tiles_s = smem_u32(gram);
         const uint32_t idesc = instr_desc(GRAM == kGramTf32x3 ? 2u : 1u, 128u, (uint32_t)A.N_mma);
-        const int L1n = A.l_max + 1;
+        const int L1n = kLmax + 1;
         auto issue = [&](int l) {
             const uint32_t d = taddr + (uint32_t)((l & 1) * A.slot_cols);
             for (int kk = 0; kk < A.nk[l]; ++kk) {
@@ -639,7 +649,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         const int n_chunks = A.N_mma / 16;
         const bool packed = A.layout == RASCAL_LAYOUT_PACKED;
         // offset of row q1 inside an l block: packed rows hold q2 >= q1 at q1 (2Q - q1 - 1) / 2 + q2
-        const int row_off = packed ? (q1 * (2 * A.Q - q1 - 1)) / 2 : q1 * A.Q;
+        const int row_off = packed ? (q1 * (2 * kQ - q1 - 1)) / 2 : q1 * kQ;
         bool ok = true;
         int gi = 0;
         for (int l = 0; l < L1n; ++l) {
@@ -653,7 +663,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                                                                         (uint32_t)((l >> 1) & 1),
                                                                         stall ? A.stall_polls : (1u << 22)));
             tc_fence_after();
-            if (done && 32 * quad < A.Q) {
+            if (done && 32 * quad < kQ) {
                 const float kl = A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f;
                 float* row = st + (l - lo) * A.per_l + row_off;
                 const uint32_t tl = taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)((l & 1) * A.slot_cols);
@@ -661,11 +671,11 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     if (packed && 16 * jb + 15 < 32 * quad) continue;  // chunk entirely below the diagonal
                     float v[16];
                     tmem_ld16(tl + 16 * jb, v);
-                    if (q1 < A.Q) {
+                    if (q1 < kQ) {
 #pragma unroll
                         for (int t = 0; t < 16; ++t) {
                             const int q2 = 16 * jb + t;
-                            if (q2 < A.Q && (!packed || q2 >= q1)) row[q2] = kl * v[t];
+                            if (q2 < kQ && (!packed || q2 >= q1)) row[q2] = kl * v[t];
                         }
                     }
                 }
@@ -733,9 +743,9 @@ static void make_plan(rascal_ctx* ctx) {
     P.smem_ps = 0;
 }
 
-template <int GRAM>
+template <int GRAM, int SHAPE = 0>
 static int set_attr() {
-    RASCAL_CUDA(cudaFuncSetAttribute(k_expansion<GRAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RASCAL_CUDA(cudaFuncSetAttribute(k_expansion<GRAM, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     return RASCAL_OK;
 }
 
@@ -757,7 +767,8 @@ int expansion_setup(rascal_ctx* ctx) {
     int st;
     if ((st = set_attr<kGramNone>()) || (st = set_attr<kGramSimt>()) || (st = set_attr<kGramSel>()) ||
         (st = set_attr<kGramBf16>()) ||
-        (st = set_attr<kGramTf32x3>()) || (st = set_attr<kGramRTf32>()) || (st = set_attr<kGramRBf16>()))
+        (st = set_attr<kGramTf32x3>()) || (st = set_attr<kGramRTf32>()) || (st = set_attr<kGramRBf16>()) ||
+        (st = set_attr<kGramSimt, 1>()) || (st = set_attr<kGramSimt, 2>()) || (st = set_attr<kGramSimt, 3>()))
         return st;
     RASCAL_CUDA(cudaStreamSynchronize(ctx->stream));
     return RASCAL_OK;
@@ -935,9 +946,30 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
     return RASCAL_OK;
 }
 
-template <int GRAM>
+static_assert(kNumExpShapes == 4, "one dispatch case per shaped instance");
+
+// index of the compiled shape whose derived sizes all equal this launch's, else 0 (the runtime-shaped kernel)
+static int exp_shape_of(const rascal_ctx* ctx, const ExpArgs& A) {
+    for (int k = 1; k < kNumExpShapes; ++k) {
+        const ExpShape& c = kExpShapes[k];
+        if (ctx->n_max != c.n_max || ctx->l_max != c.l_max || ctx->n_species != c.S) continue;
+        const bool same = A.n_max == c.n_max && A.l_max == c.l_max && A.S == c.S && A.Q == c.n_max * c.S &&
+                          A.n_lm == (c.l_max + 1) * (c.l_max + 1) && A.n_pad == exp_npad(c.n_max) &&
+                          A.F_pad == (c.l_max + 1) * exp_npad(c.n_max) && A.F == (c.l_max + 1) * c.n_max &&
+                          A.Ly == exp_ly(c.l_max) && A.Qp == exp_qp(c.n_max * c.S) &&
+                          A.T_s == exp_ts(c.n_max, c.l_max) && A.W_s == (exp_ts(c.n_max, c.l_max) + 31) / 32 &&
+                          A.S_c == exp_sc(c.n_max, c.l_max, c.S) &&
+                          A.rounds == (c.S + A.S_c - 1) / A.S_c && A.chunk == exp_chunk(c.n_max, c.l_max);
+        bool lp_same = true;
+        for (int l = 0; l <= c.l_max; ++l) lp_same = lp_same && A.lp[l] == exp_lp(l);
+        if (same && lp_same) return k;
+    }
+    return 0;
+}
+
+template <int GRAM, int SHAPE = 0>
 static int launch_expansion(rascal_ctx* ctx, const ExpArgs& A, int n_atoms, int threads, size_t smem) {
-    k_expansion<GRAM><<<n_atoms, threads, smem, ctx->stream>>>(A);
+    k_expansion<GRAM, SHAPE><<<n_atoms, threads, smem, ctx->stream>>>(A);
     RASCAL_LAUNCH_CHECK("k_expansion");
     return RASCAL_OK;
 }
@@ -1045,7 +1077,14 @@ extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int6
     size_t smem;
     int threads;
     if ((st = make_gram(ctx, mode, layout, d_ps, A, &smem, &threads))) return st;
-    if (mode == kGramSimt) return launch_expansion<kGramSimt>(ctx, A, sys->n_atoms, threads, smem);
+    if (mode == kGramSimt) {
+        switch (exp_shape_of(ctx, A)) {
+            case 1: return launch_expansion<kGramSimt, 1>(ctx, A, sys->n_atoms, threads, smem);
+            case 2: return launch_expansion<kGramSimt, 2>(ctx, A, sys->n_atoms, threads, smem);
+            case 3: return launch_expansion<kGramSimt, 3>(ctx, A, sys->n_atoms, threads, smem);
+            default: return launch_expansion<kGramSimt>(ctx, A, sys->n_atoms, threads, smem);
+        }
+    }
     if (mode == kGramBf16) return launch_expansion<kGramBf16>(ctx, A, sys->n_atoms, threads, smem);
     return launch_expansion<kGramTf32x3>(ctx, A, sys->n_atoms, threads, smem);
 }

@@ -133,12 +133,23 @@ __global__ void k_wsym(int S, int L1, int Q, int Qw, int ps_norm, const float* _
 //      contraction s = sum_lm Y sum_n chat (f I)', w = sum_lm dY/du sum_n chat f I (one warp per pair, lanes over
 //      lm, warp-shuffle reduction);
 //      dE/dr_ji, the force scatter and the virial (one thread per pair).
+template <int SHAPE = 0>
 __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A) {
+    // hyper shape: compile-time constants for the instantiated shapes (kExpShapes), the launch arguments otherwise
+    constexpr ExpShape Cs = kExpShapes[SHAPE];
+    const int kNmax = SHAPE ? Cs.n_max : A.n_max, kLmax = SHAPE ? Cs.l_max : A.l_max;
+    const int kQ = SHAPE ? Cs.n_max * Cs.S : A.Q, kNlm = SHAPE ? (Cs.l_max + 1) * (Cs.l_max + 1) : A.n_lm;
+    const int kNpad = SHAPE ? exp_npad(Cs.n_max) : A.n_pad, kFpad = SHAPE ? (Cs.l_max + 1) * exp_npad(Cs.n_max) : A.F_pad;
+    const int kF = SHAPE ? (Cs.l_max + 1) * Cs.n_max : A.F, kQw = SHAPE ? (Cs.n_max * Cs.S + 3) / 4 * 4 : A.Qw;
+    const int kLpAdj = SHAPE ? exp_lp(Cs.l_max + 1) : A.Lp_adj;
+    const int kAdjTasks = SHAPE ? (Cs.n_max * Cs.S + 3) / 4 * (exp_lp(Cs.l_max + 1) / 4) : A.n_adj_tasks;
+    // prefix counts of the adjoint tile tasks per l: ceil(Q / 4) ceil((2l' + 1) / 4) summed over l' < l
+    auto adj_pref = [&](int l) { return SHAPE ? (kQ + 3) / 4 * (exp_lp(l) / 4) : A.adj_pref[l]; };
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int chunk = A.chunk;
-    const int QN = A.Q * A.n_lm;
+    const int QN = kQ * kNlm;
     const int QN4 = (QN + 3) & ~3;                            // keeps the float4 arrays 16-byte aligned
-    const int Yp = A.n_lm | 1;                                // odd pitch: conflict-free float4 rows
+    const int Yp = kNlm | 1;                                // odd pitch: conflict-free float4 rows
     float* s_H = reinterpret_cast<float*>(smem_raw);          // chat [Q][n_lm]
     // the coefficients are needed only by the adjoint, before the pair loop: they share the pair area
     float* s_C = s_H + QN4;                                   // [Q][n_lm], or [Q][Lp_adj] padded per l (tiled adjoint)
@@ -146,12 +157,12 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
     float4* s_Yv = s_vec + chunk;                             // [chunk][Yp]  (Y, dY/dux, dY/duy, dY/duz)
     float4* s_acc = s_Yv + (size_t)chunk * Yp;                // [chunk]      (s, wx, wy, wz)
     float2* s_GD = reinterpret_cast<float2*>(s_acc + chunk);  // [chunk][F_pad]  (f I, (f I)')
-    float* s_fc = reinterpret_cast<float*>(s_GD + (size_t)chunk * A.F_pad);
+    float* s_fc = reinterpret_cast<float*>(s_GD + (size_t)chunk * kFpad);
     float* s_dfc = s_fc + chunk;
     int* s_spc = reinterpret_cast<int*>(s_dfc + chunk);
     int* s_j = s_spc + chunk;
     int* s_lofm = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(s_vec) + A.aux_off);  // [n_lm] l of lm
-    int* s_fmap = s_lofm + A.n_lm;                            // [F_pad]
+    int* s_fmap = s_lofm + kNlm;                            // [F_pad]
     __shared__ double red[kGradThreads / 32][12];
     __shared__ int s_sid;
 
@@ -166,43 +177,43 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
         s_sid = lo;
     }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int L1 = A.l_max + 1;
-    for (int lm = tid; lm < A.n_lm; lm += blockDim.x) s_lofm[lm] = (int)sqrtf((float)lm);  // l with l^2 <= lm
-    for (int t = tid; t < A.F_pad; t += blockDim.x) s_fmap[t] = A.fmap[t];
+    const int L1 = kLmax + 1;
+    for (int lm = tid; lm < kNlm; lm += blockDim.x) s_lofm[lm] = (int)sqrtf((float)lm);  // l with l^2 <= lm
+    for (int t = tid; t < kFpad; t += blockDim.x) s_fmap[t] = A.fmap[t];
     const int lab_i = A.species[i];
     const int a_i = (lab_i >= 0 && lab_i < 256) ? A.lut[lab_i] : -1;
     const float* Gp = A.grad_ps ? A.grad_ps + (int64_t)i * A.Fp : (a_i >= 0 ? A.weights + (int64_t)a_i * A.Fp : nullptr);
     const float* c = A.coeffs + (int64_t)i * QN;
-    const int Q = A.Q, n_lm = A.n_lm, Qpk = Q * (Q + 1) / 2;
+    const int Q = kQ, n_lm = kNlm, Qpk = Q * (Q + 1) / 2;
     if (A.wsym) {
         // adjoint as 4 x 4 register tiles of chat_l = Ws_l C_l: C staged with every l block padded to a multiple of
         // 4 columns (zeros), so that tiles load float4 rows of C and of the dense symmetric weights
-        const int Lq = A.Lp_adj;
+        const int Lq = kLpAdj;
         for (int e = tid; e < Q * Lq; e += blockDim.x) s_C[e] = 0.0f;  // padding columns read as zero
         __syncthreads();
         for (int q = warp; q < Q; q += nwarps)  // per row: lanes over lm
             for (int lm = lane; lm < n_lm; lm += 32) {
                 const int l = s_lofm[lm];
-                cp_async4(s_C + q * Lq + A.lp[l] + (lm - l * l), c + q * n_lm + lm);
+                cp_async4(s_C + q * Lq + exp_lp(l) + (lm - l * l), c + q * n_lm + lm);
             }
         cp_async_wait_all();
         __syncthreads();
         const int QT = (Q + 3) >> 2;
-        const float* Wsa = A.wsym + (int64_t)(a_i < 0 ? 0 : a_i) * L1 * Q * A.Qw;
-        for (int t = tid; t < A.n_adj_tasks && a_i >= 0; t += blockDim.x) {
+        const float* Wsa = A.wsym + (int64_t)(a_i < 0 ? 0 : a_i) * L1 * Q * kQw;
+        for (int t = tid; t < kAdjTasks && a_i >= 0; t += blockDim.x) {
             int l = 0;
-            while (A.adj_pref[l + 1] <= t) ++l;
-            const int r = t - A.adj_pref[l];
+            while (adj_pref(l + 1) <= t) ++l;
+            const int r = t - adj_pref(l);
             const int st = r / QT, qt = r - st * QT;
-            const float* Wl = Wsa + (int64_t)l * Q * A.Qw + 4 * qt;
-            const float* Cl = s_C + A.lp[l] + 4 * st;
+            const float* Wl = Wsa + (int64_t)l * Q * kQw + 4 * qt;
+            const float* Cl = s_C + exp_lp(l) + 4 * st;
             float acc[4][4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
             for (int k = 0; k < Q; ++k) {
-                const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wl + k * A.Qw));
+                const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wl + k * kQw));
                 const float4 c4 = *reinterpret_cast<const float4*>(Cl + k * Lq);
                 const float ww[4] = {w4.x, w4.y, w4.z, w4.w}, cc[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
@@ -285,11 +296,11 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
         // radial values and slopes: one warp per pair, lanes over padded (l, n); the warps without a Y chain first
         for (int p = nwarps - 1 - warp; p < nc; p += nwarps) {
             const float f = s_fc[p], df = s_dfc[p];
-            float2* gd = s_GD + p * A.F_pad;
+            float2* gd = s_GD + p * kFpad;
             if (A.pre_G) {
-                const float* pg = A.pre_G + (pos + p) * A.F;
-                const float* pd = A.pre_D + (pos + p) * A.F;
-                for (int fp = lane; fp < A.F_pad; fp += 32) {
+                const float* pg = A.pre_G + (pos + p) * kF;
+                const float* pd = A.pre_D + (pos + p) * kF;
+                for (int fp = lane; fp < kFpad; fp += 32) {
                     const int col = s_fmap[fp];
                     const float g = col >= 0 ? __ldg(pg + col) : 0.0f, dg = col >= 0 ? __ldg(pd + col) : 0.0f;
                     gd[fp] = make_float2(f * g, df * g + f * dg);
@@ -298,8 +309,8 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
                 const float x = s_vec[p].w * A.inv_delta;
                 const int k = min(max((int)x, 0), A.M - 1);
                 const float u = x - (float)k;
-                const float4* trow = A.table + k * A.F;
-                for (int fp = lane; fp < A.F_pad; fp += 32) {
+                const float4* trow = A.table + k * kF;
+                for (int fp = lane; fp < kFpad; fp += 32) {
                     const int col = s_fmap[fp];
                     const float4 cf = col >= 0 ? __ldg(trow + col) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     const float g = fmaf(u, fmaf(u, fmaf(u, cf.w, cf.z), cf.y), cf.x);
@@ -355,15 +366,15 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
         for (int p = warp; p < nc; p += nwarps) {
             const int a = s_spc[p];
             if (a < 0) continue;  // warp-uniform
-            const float* H = s_H + a * A.n_max * n_lm;
-            const float2* gd = s_GD + p * A.F_pad;
+            const float* H = s_H + a * kNmax * n_lm;
+            const float2* gd = s_GD + p * kFpad;
             const float4* Yrow = s_Yv + p * Yp;
             float S = 0.0f, Wx = 0.0f, Wy = 0.0f, Wz = 0.0f;
             for (int lm = lane; lm < n_lm; lm += 32) {
-                const float2* g = gd + s_lofm[lm] * A.n_pad;
+                const float2* g = gd + s_lofm[lm] * kNpad;
                 const float* h = H + lm;
                 float uu = 0.0f, vv = 0.0f;
-                for (int n = 0; n < A.n_max; ++n) {
+                for (int n = 0; n < kNmax; ++n) {
                     const float hv = h[n * n_lm];
                     const float2 x = g[n];
                     vv = fmaf(hv, x.x, vv);
@@ -453,7 +464,10 @@ static size_t grad_smem(const rascal_ctx* ctx, int chunk, bool tiled) {
 
 int gradients_setup(rascal_ctx* ctx) {
     RASCAL_CUDA(upload_ylm_constants(ctx->stream));
-    RASCAL_CUDA(cudaFuncSetAttribute(k_gradients, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RASCAL_CUDA(cudaFuncSetAttribute(k_gradients<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RASCAL_CUDA(cudaFuncSetAttribute(k_gradients<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RASCAL_CUDA(cudaFuncSetAttribute(k_gradients<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RASCAL_CUDA(cudaFuncSetAttribute(k_gradients<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     return RASCAL_OK;
 }
 
@@ -559,7 +573,22 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
     const size_t smem = grad_smem(ctx, chunk, A.wsym != nullptr);
     if (smem > 220 * 1024) return set_error(RASCAL_E_UNSUPPORTED, "hypers too large for the gradient kernel");
     if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, true, &A.pre_G, &A.pre_D))) return st;
-    k_gradients<<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A);
+    // a compiled instance for the hyper shape when the plan's sizes match it (kExpShapes), else the generic kernel
+    int shape = 0;
+    for (int k = 1; k < kNumExpShapes && !shape; ++k) {
+        const ExpShape& c = kExpShapes[k];
+        if (ctx->n_max == c.n_max && ctx->l_max == c.l_max && ctx->n_species == c.S && P.n_pad == exp_npad(c.n_max) &&
+            P.F_pad == (c.l_max + 1) * exp_npad(c.n_max) && P.Lp == exp_lp(c.l_max + 1) && ctx->Q == c.n_max * c.S &&
+            ctx->n_lm == (c.l_max + 1) * (c.l_max + 1) && ctx->F == (c.l_max + 1) * c.n_max && (!A.wsym || A.Qw == (ctx->Q + 3) / 4 * 4))
+            shape = k;
+    }
+    static_assert(kNumExpShapes == 4, "one launch case per shaped instance");
+    switch (shape) {
+        case 1: k_gradients<1><<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A); break;
+        case 2: k_gradients<2><<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A); break;
+        case 3: k_gradients<3><<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A); break;
+        default: k_gradients<0><<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A); break;
+    }
     RASCAL_LAUNCH_CHECK("k_gradients");
     const int64_t n3 = 3 * (int64_t)sys->n_atoms;
     k_forces_f64<<<(unsigned)std::min<int64_t>((n3 + 255) / 256, 8192), 256, 0, ctx->stream>>>(n3, f32, d_forces);

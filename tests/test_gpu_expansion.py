@@ -136,3 +136,46 @@ def test_fused_soap_equals_separate_calls(rg):
     c2, p2 = calc.soap(ds, pairs)
     assert np.array_equal(c1.cpu().numpy(), c2.cpu().numpy())
     assert np.max(np.abs(p1.cpu().numpy() - p2.cpu().numpy())) <= 1e-6 * np.max(np.abs(p1.cpu().numpy()))
+
+
+@pytest.mark.parametrize("hyp_name", ["HYPERS_BATCH", "HYPERS_LARGE", "HYPERS_DIFF"])
+def test_shaped_instances_match_oracle(rg, hyp_name):
+    # the hyper shapes with their own compiled instance of the fused FP32 kernel (compile-time n_max, l_max and
+    # species count): fused c and p, PACKED and FULL, against the oracle, with a crowded centre (more pairs than one
+    # staged chunk) and an isolated atom; the same system through the separate calls as a second check
+    import synth
+
+    hyp = dict(getattr(synth.structures, hyp_name))
+    rng = np.random.Generator(np.random.PCG64(31))
+    L = 30.0
+    pos = np.concatenate([random_cell_atoms(70, np.eye(3) * 9.0, 1.05, rng) + 2.0, [[25.0, 25.0, 25.0]]])
+    labels = hyp["species"]
+    spe = np.asarray(labels, np.int32)[rng.integers(0, len(labels), len(pos))]
+    s = System(pos, spe, (np.eye(3) * L)[None], np.zeros((1, 3), np.int32), np.array([0, len(pos)], np.int32), hyp)
+    h = osoap.Hypers(**hyp)
+    c_ref = osoap.spherical_expansion(s, h)
+    calc = rg.SoapCalculator(**hyp)
+    ds = rg.DeviceSystem.from_numpy(s)
+    pairs = calc.neighbours(ds)
+    assert np.diff(pairs.offsets.cpu().numpy()).max() > 32
+    for layout in ("packed", "full"):
+        c, p = calc.soap(ds, pairs, layout=layout)
+        p_sep = calc.power_spectrum(calc.spherical_expansion(ds, pairs), layout=layout)
+        calc.sync()
+        c, p, p_sep = c.cpu().numpy(), p.cpu().numpy(), p_sep.cpu().numpy()
+        p_ref = osoap.power_spectrum(c_ref, h, layout).reshape(len(pos), h.l_max + 1, -1)
+        assert block_rel_err(c, c_ref, 2) <= TOL
+        assert block_rel_err(ps_blocks(p, h.l_max), p_ref, 2) <= TOL, layout
+        assert block_rel_err(ps_blocks(p_sep, h.l_max), p_ref, 2) <= TOL, layout
+        assert np.all(c[-1] == 0.0) and np.all(p[-1] == 0.0)
+    # forces and virial of the linear energy model through the gradient kernel's instance for the same shape
+    import torch
+
+    from paper_2101_08814_gb300.autograd import LinearSoapEnergy
+    from synth import linear_weights
+
+    w = linear_weights(h.n_species, h.n_features("packed"), seed=4)
+    _, f, v = LinearSoapEnergy(calc, torch.tensor(w, dtype=torch.float32))(ds)
+    F_ref, V_ref = osoap.energy_gradients(s, h, w)
+    assert np.max(np.abs(f.cpu().numpy() - F_ref)) <= 1e-4 * np.max(np.abs(F_ref))
+    assert np.max(np.abs(v.cpu().numpy() - V_ref)) <= 1e-4 * np.max(np.abs(V_ref))
