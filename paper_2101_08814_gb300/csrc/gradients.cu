@@ -74,6 +74,8 @@ struct GradArgs {
     const float* weights;   // [S][Fp] or NULL
     const float* wsym;      // weights only: k_l (W_l + W_l^T) per species and l, dense [S][L1][Q][Qw] (Qw = ceil4(Q))
     int Qw, Lp_adj, n_adj_tasks;
+    int w_tiled;            // per-centre dE/dp: tiled adjoint with one dense l block staged in shared memory
+    int w_off;              // bytes from the pair area to that block
     int aux_off;            // bytes from the pair area to the small tables (past both the pair area and C)
     int adj_pref[kMaxLMax + 2];  // prefix counts of the adjoint tile tasks per l
     float* forces;          // FP32 accumulation, converted to the FP64 output afterwards
@@ -185,7 +187,36 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
     const float* Gp = A.grad_ps ? A.grad_ps + (int64_t)i * A.Fp : (a_i >= 0 ? A.weights + (int64_t)a_i * A.Fp : nullptr);
     const float* c = A.coeffs + (int64_t)i * QN;
     const int Q = kQ, n_lm = kNlm, Qpk = Q * (Q + 1) / 2;
-    if (A.wsym) {
+    // one 4 x 4 register tile of chat_l = Ws_l C_l (rows 4 qt.., columns 4 st.. of the l block), Ws_l dense and
+    // symmetric with row pitch Qw (in global memory for the linear model, in shared memory for a per-centre dE/dp)
+    auto adjoint_tile = [&](const float* Wl, const float* Cl, int Lq, int l, int qt, int st, bool w_global) {
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+        for (int k = 0; k < kQ; ++k) {
+            const float4 w4 = w_global ? __ldg(reinterpret_cast<const float4*>(Wl + k * kQw))
+                                       : *reinterpret_cast<const float4*>(Wl + k * kQw);
+            const float4 c4 = *reinterpret_cast<const float4*>(Cl + k * Lq);
+            const float ww[4] = {w4.x, w4.y, w4.z, w4.w}, cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ww[u], cc[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = 4 * qt + u;
+            if (q >= kQ) break;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int sx = 4 * st + v;
+                if (sx <= 2 * l) s_H[q * kNlm + l * l + sx] = acc[u][v];
+            }
+        }
+    };
+    if (A.wsym || A.w_tiled) {
         // adjoint as 4 x 4 register tiles of chat_l = Ws_l C_l: C staged with every l block padded to a multiple of
         // 4 columns (zeros), so that tiles load float4 rows of C and of the dense symmetric weights
         const int Lq = kLpAdj;
@@ -199,41 +230,42 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
         cp_async_wait_all();
         __syncthreads();
         const int QT = (Q + 3) >> 2;
-        const float* Wsa = A.wsym + (int64_t)(a_i < 0 ? 0 : a_i) * L1 * Q * kQw;
-        for (int t = tid; t < kAdjTasks && a_i >= 0; t += blockDim.x) {
-            int l = 0;
-            while (adj_pref(l + 1) <= t) ++l;
-            const int r = t - adj_pref(l);
-            const int st = r / QT, qt = r - st * QT;
-            const float* Wl = Wsa + (int64_t)l * Q * kQw + 4 * qt;
-            const float* Cl = s_C + exp_lp(l) + 4 * st;
-            float acc[4][4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
-            for (int k = 0; k < Q; ++k) {
-                const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wl + k * kQw));
-                const float4 c4 = *reinterpret_cast<const float4*>(Cl + k * Lq);
-                const float ww[4] = {w4.x, w4.y, w4.z, w4.w}, cc[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ww[u], cc[v], acc[u][v]);
+        if (A.wsym) {  // linear model: the species' dense blocks, shared by all centres, from global memory (L2)
+            const float* Wsa = A.wsym + (int64_t)(a_i < 0 ? 0 : a_i) * L1 * Q * kQw;
+            for (int t = tid; t < kAdjTasks && a_i >= 0; t += blockDim.x) {
+                int l = 0;
+                while (adj_pref(l + 1) <= t) ++l;
+                const int r = t - adj_pref(l);
+                const int st = r / QT, qt = r - st * QT;
+                adjoint_tile(Wsa + (int64_t)l * Q * kQw + 4 * qt, s_C + exp_lp(l) + 4 * st, Lq, l, qt, st, true);
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = 4 * qt + u;
-                if (q >= Q) break;
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int sx = 4 * st + v;
-                    if (sx <= 2 * l) s_H[q * n_lm + l * l + sx] = acc[u][v];
+            if (a_i < 0)
+                for (int e = tid; e < QN; e += blockDim.x) s_H[e] = 0.0f;
+        } else {  // this centre's dE/dp: one l block at a time, expanded to k_l (W_l + W_l^T) in shared memory
+            float* s_W = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(s_vec) + A.w_off);  // [Q][Qw]
+            for (int l = 0; l < L1; ++l) {
+                const float kl = A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f;
+                const float* Wp = Gp + (int64_t)l * Qpk;
+                for (int e = tid; e < Q * kQw; e += blockDim.x) {
+                    const int k = e / kQw, q = e - k * kQw;
+                    float v = 0.0f;
+                    if (q < Q) {  // the packed entry (lo <= hi) sits at lo (2Q - lo - 1) / 2 + hi
+                        const int lo = min(q, k), hi = max(q, k);
+                        v = __ldg(Wp + (lo * (2 * Q - lo - 1)) / 2 + hi);
+                        if (q == k) v *= 2.0f;
+                        v *= kl;
+                    }
+                    s_W[e] = v;
                 }
+                __syncthreads();
+                const int ntl = QT * ((2 * l + 1 + 3) / 4);
+                for (int t = tid; t < ntl; t += blockDim.x) {
+                    const int st = t / QT, qt = t - st * QT;
+                    adjoint_tile(s_W + 4 * qt, s_C + exp_lp(l) + 4 * st, Lq, l, qt, st, false);
+                }
+                __syncthreads();
             }
         }
-        if (a_i < 0)
-            for (int e = tid; e < QN; e += blockDim.x) s_H[e] = 0.0f;
     } else {
     for (int e = tid; e < QN; e += blockDim.x) cp_async4(s_C + e, c + e);
     cp_async_wait_all();
@@ -456,9 +488,16 @@ static size_t grad_aux_off(const rascal_ctx* ctx, int chunk, bool tiled) {
     return align_up(std::max(pair_area, sizeof(float) * QL4), 16);
 }
 
-static size_t grad_smem(const rascal_ctx* ctx, int chunk, bool tiled) {
+// bytes from the pair area to the dense weight block of the per-centre tiled adjoint (behind the small tables)
+static size_t grad_w_off(const rascal_ctx* ctx, int chunk) {
+    return align_up(grad_aux_off(ctx, chunk, true) + sizeof(int) * (ctx->n_lm + ctx->plan.F_pad), 16);
+}
+
+static size_t grad_smem(const rascal_ctx* ctx, int chunk, bool tiled, bool w_block = false) {
     const ExpPlan& P = ctx->plan;
     const size_t QN4 = ((size_t)ctx->Q * ctx->n_lm + 3) / 4 * 4;
+    if (w_block)
+        return sizeof(float) * QN4 + grad_w_off(ctx, chunk) + sizeof(float) * ctx->Q * ((ctx->Q + 3) / 4 * 4) + 64;
     return sizeof(float) * QN4 + grad_aux_off(ctx, chunk, tiled) + sizeof(int) * (ctx->n_lm + P.F_pad) + 64;
 }
 
@@ -565,12 +604,29 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
         for (int l = L1; l < kMaxLMax + 1; ++l) A.adj_pref[l + 1] = A.adj_pref[l];
         A.n_adj_tasks = A.adj_pref[L1];
     }
-    // the largest chunk (<= 32: warp 0 runs the per-pair phase) that keeps five CTAs per SM (48 registers)
+    // the largest chunk (<= 32: warp 0 runs the per-pair phase) that keeps five CTAs per SM (48 registers); a
+    // per-centre dE/dp takes the tiled adjoint with one dense l block in shared memory when four CTAs per SM keep a
+    // chunk of at least 8 pairs, else the per-element adjoint
+    A.w_tiled = 0;
+    A.w_off = 0;
     int chunk = 32;
-    while (chunk > 1 && grad_smem(ctx, chunk, A.wsym != nullptr) > 44 * 1024) --chunk;
+    if (!d_weights) {
+        while (chunk > 8 && grad_smem(ctx, chunk, true, true) > 54 * 1024) --chunk;
+        if (grad_smem(ctx, chunk, true, true) <= 54 * 1024) {
+            A.w_tiled = 1;
+            A.Qw = Qw;
+            A.Lp_adj = P.Lp;
+            A.w_off = (int)grad_w_off(ctx, chunk);
+        } else {
+            chunk = 32;
+        }
+    }
+    const bool tiled = A.wsym != nullptr || A.w_tiled;
+    if (!A.w_tiled)
+        while (chunk > 1 && grad_smem(ctx, chunk, tiled) > 44 * 1024) --chunk;
     A.chunk = chunk;
-    A.aux_off = (int)grad_aux_off(ctx, chunk, A.wsym != nullptr);
-    const size_t smem = grad_smem(ctx, chunk, A.wsym != nullptr);
+    A.aux_off = (int)grad_aux_off(ctx, chunk, tiled);
+    const size_t smem = grad_smem(ctx, chunk, tiled, A.w_tiled != 0);
     if (smem > 220 * 1024) return set_error(RASCAL_E_UNSUPPORTED, "hypers too large for the gradient kernel");
     if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, true, &A.pre_G, &A.pre_D))) return st;
     // a compiled instance for the hyper shape when the plan's sizes match it (kExpShapes), else the generic kernel
