@@ -768,7 +768,10 @@ int expansion_setup(rascal_ctx* ctx) {
     if ((st = set_attr<kGramNone>()) || (st = set_attr<kGramSimt>()) || (st = set_attr<kGramSel>()) ||
         (st = set_attr<kGramBf16>()) ||
         (st = set_attr<kGramTf32x3>()) || (st = set_attr<kGramRTf32>()) || (st = set_attr<kGramRBf16>()) ||
-        (st = set_attr<kGramSimt, 1>()) || (st = set_attr<kGramSimt, 2>()) || (st = set_attr<kGramSimt, 3>()))
+        (st = set_attr<kGramSimt, 1>()) || (st = set_attr<kGramSimt, 2>()) || (st = set_attr<kGramSimt, 3>()) ||
+        (st = set_attr<kGramNone, 1>()) || (st = set_attr<kGramNone, 2>()) || (st = set_attr<kGramNone, 3>()) ||
+        (st = set_attr<kGramBf16, 1>()) || (st = set_attr<kGramBf16, 2>()) || (st = set_attr<kGramBf16, 3>()) ||
+        (st = set_attr<kGramRTf32, 1>()) || (st = set_attr<kGramRTf32, 2>()) || (st = set_attr<kGramRTf32, 3>()))
         return st;
     RASCAL_CUDA(cudaStreamSynchronize(ctx->stream));
     return RASCAL_OK;
@@ -948,15 +951,16 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
 
 static_assert(kNumExpShapes == 4, "one dispatch case per shaped instance");
 
-// index of the compiled shape whose derived sizes all equal this launch's, else 0 (the runtime-shaped kernel)
-static int exp_shape_of(const rascal_ctx* ctx, const ExpArgs& A) {
+// index of the compiled shape whose derived sizes all equal this launch's, else 0 (the runtime-shaped kernel); the
+// CT row pitch Qp is set (and checked) only for the forms that hold c transposed in shared memory
+static int exp_shape_of(const rascal_ctx* ctx, const ExpArgs& A, bool with_qp) {
     for (int k = 1; k < kNumExpShapes; ++k) {
         const ExpShape& c = kExpShapes[k];
         if (ctx->n_max != c.n_max || ctx->l_max != c.l_max || ctx->n_species != c.S) continue;
         const bool same = A.n_max == c.n_max && A.l_max == c.l_max && A.S == c.S && A.Q == c.n_max * c.S &&
                           A.n_lm == (c.l_max + 1) * (c.l_max + 1) && A.n_pad == exp_npad(c.n_max) &&
                           A.F_pad == (c.l_max + 1) * exp_npad(c.n_max) && A.F == (c.l_max + 1) * c.n_max &&
-                          A.Ly == exp_ly(c.l_max) && A.Qp == exp_qp(c.n_max * c.S) &&
+                          A.Ly == exp_ly(c.l_max) && (!with_qp || A.Qp == exp_qp(c.n_max * c.S)) &&
                           A.T_s == exp_ts(c.n_max, c.l_max) && A.W_s == (exp_ts(c.n_max, c.l_max) + 31) / 32 &&
                           A.S_c == exp_sc(c.n_max, c.l_max, c.S) &&
                           A.rounds == (c.S + A.S_c - 1) / A.S_c && A.chunk == exp_chunk(c.n_max, c.l_max);
@@ -972,6 +976,17 @@ static int launch_expansion(rascal_ctx* ctx, const ExpArgs& A, int n_atoms, int 
     k_expansion<GRAM, SHAPE><<<n_atoms, threads, smem, ctx->stream>>>(A);
     RASCAL_LAUNCH_CHECK("k_expansion");
     return RASCAL_OK;
+}
+
+// the compiled instance for the launch's hyper shape, else the runtime-shaped kernel
+template <int GRAM>
+static int launch_shaped(rascal_ctx* ctx, const ExpArgs& A, int n_atoms, int threads, size_t smem) {
+    switch (exp_shape_of(ctx, A, GRAM == kGramSimt)) {
+        case 1: return launch_expansion<GRAM, 1>(ctx, A, n_atoms, threads, smem);
+        case 2: return launch_expansion<GRAM, 2>(ctx, A, n_atoms, threads, smem);
+        case 3: return launch_expansion<GRAM, 3>(ctx, A, n_atoms, threads, smem);
+        default: return launch_expansion<GRAM>(ctx, A, n_atoms, threads, smem);
+    }
 }
 
 int power_spectrum_tc(rascal_ctx* ctx, int64_t n_centres, const float* d_coeffs, int precision, int layout, float* d_ps) {
@@ -1002,7 +1017,7 @@ extern "C" int rascal_spherical_expansion(rascal_ctx* ctx, const rascal_system* 
     ExpArgs A = make_args(ctx, sys, d_offsets, d_nbr_j, d_rij, d_coeffs);
     const float* pre_D;
     if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, false, &A.pre_G, &pre_D))) return st;
-    return launch_expansion<kGramNone>(ctx, A, sys->n_atoms, ctx->plan.threads, ctx->plan.smem);
+    return launch_shaped<kGramNone>(ctx, A, sys->n_atoms, ctx->plan.threads, ctx->plan.smem);
 }
 
 // PACKED feature index -> (l | q1 << 8 | q2 << 16); out-of-range indices flag an error and decode to l = 255 (zero)
@@ -1069,7 +1084,7 @@ extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int6
         size_t smem_r;
         int threads_r;
         st = make_gram(ctx, kGramRTf32, layout, d_ps, R, &smem_r, &threads_r);
-        if (st == RASCAL_OK) return launch_expansion<kGramRTf32>(ctx, R, sys->n_atoms, threads_r, smem_r);
+        if (st == RASCAL_OK) return launch_shaped<kGramRTf32>(ctx, R, sys->n_atoms, threads_r, smem_r);
         if (st != RASCAL_E_UNSUPPORTED) return st;
         clear_error();
     }
@@ -1077,14 +1092,7 @@ extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int6
     size_t smem;
     int threads;
     if ((st = make_gram(ctx, mode, layout, d_ps, A, &smem, &threads))) return st;
-    if (mode == kGramSimt) {
-        switch (exp_shape_of(ctx, A)) {
-            case 1: return launch_expansion<kGramSimt, 1>(ctx, A, sys->n_atoms, threads, smem);
-            case 2: return launch_expansion<kGramSimt, 2>(ctx, A, sys->n_atoms, threads, smem);
-            case 3: return launch_expansion<kGramSimt, 3>(ctx, A, sys->n_atoms, threads, smem);
-            default: return launch_expansion<kGramSimt>(ctx, A, sys->n_atoms, threads, smem);
-        }
-    }
-    if (mode == kGramBf16) return launch_expansion<kGramBf16>(ctx, A, sys->n_atoms, threads, smem);
+    if (mode == kGramSimt) return launch_shaped<kGramSimt>(ctx, A, sys->n_atoms, threads, smem);
+    if (mode == kGramBf16) return launch_shaped<kGramBf16>(ctx, A, sys->n_atoms, threads, smem);
     return launch_expansion<kGramTf32x3>(ctx, A, sys->n_atoms, threads, smem);
 }

@@ -168,6 +168,15 @@ def test_shaped_instances_match_oracle(rg, hyp_name):
         assert block_rel_err(ps_blocks(p, h.l_max), p_ref, 2) <= TOL, layout
         assert block_rel_err(ps_blocks(p_sep, h.l_max), p_ref, 2) <= TOL, layout
         assert np.all(c[-1] == 0.0) and np.all(p[-1] == 0.0)
+    # the tensor-core forms and the coefficients-only call have their own instances for these shapes
+    c_only = calc.spherical_expansion(ds, pairs).cpu().numpy()
+    assert block_rel_err(c_only, c_ref, 2) <= TOL
+    p_ref = osoap.power_spectrum(c_ref, h, "packed").reshape(len(pos), h.l_max + 1, -1)
+    for prec, tol in (("tf32x3", TOL), ("bf16", 2.0 ** -7)):
+        c_tc, p_tc = calc.soap(ds, pairs, precision=prec)
+        calc.sync()
+        assert block_rel_err(c_tc.cpu().numpy(), c_ref, 2) <= TOL, prec
+        assert block_rel_err(ps_blocks(p_tc.cpu().numpy(), h.l_max), p_ref, 2) <= tol, prec
     # forces and virial of the linear energy model through the gradient kernel's instance for the same shape
     import torch
 
