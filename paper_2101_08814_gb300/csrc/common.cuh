@@ -68,13 +68,13 @@ struct Arena {
 struct LsoapTable;  // lambda-SOAP coupling tables (lambda_soap.cu)
 
 // Hyper shapes with their own compiled instances of the fused FP32 kernel (expansion.cu) and the gradient kernel
-// (gradients.cu): the batch, large and diff workloads' n_max, l_max and species count. Index 0 stands for the
+// (gradients.cu): the batch, large, diff and MLP workloads' n_max, l_max and species count. Index 0 stands for the
 // runtime-shaped kernels, which serve every other shape. The derived sizes below mirror the host plan (make_plan,
 // make_gram); the host launches a shaped instance only when every one of them equals the plan's value.
 struct ExpShape {
     int n_max, l_max, S;
 };
-constexpr ExpShape kExpShapes[] = {{0, 0, 0}, {12, 9, 4}, {10, 8, 3}, {8, 6, 2}};
+constexpr ExpShape kExpShapes[] = {{0, 0, 0}, {12, 9, 4}, {10, 8, 3}, {8, 6, 2}, {16, 12, 8}};
 constexpr int kNumExpShapes = sizeof(kExpShapes) / sizeof(kExpShapes[0]);
 constexpr int exp_npad(int n_max) { return (n_max + 3) / 4 * 4; }
 // Y row offset of l: sum over l' < l of ceil4(2l' + 1), i.e. 4 k (k + 1) for l = 2k and 4 (k + 1)^2 for l = 2k + 1

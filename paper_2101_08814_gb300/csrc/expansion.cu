@@ -771,7 +771,10 @@ int expansion_setup(rascal_ctx* ctx) {
         (st = set_attr<kGramSimt, 1>()) || (st = set_attr<kGramSimt, 2>()) || (st = set_attr<kGramSimt, 3>()) ||
         (st = set_attr<kGramNone, 1>()) || (st = set_attr<kGramNone, 2>()) || (st = set_attr<kGramNone, 3>()) ||
         (st = set_attr<kGramBf16, 1>()) || (st = set_attr<kGramBf16, 2>()) || (st = set_attr<kGramBf16, 3>()) ||
-        (st = set_attr<kGramRTf32, 1>()) || (st = set_attr<kGramRTf32, 2>()) || (st = set_attr<kGramRTf32, 3>()))
+        (st = set_attr<kGramRTf32, 1>()) || (st = set_attr<kGramRTf32, 2>()) || (st = set_attr<kGramRTf32, 3>()) ||
+        (st = set_attr<kGramSel, 1>()) || (st = set_attr<kGramSel, 2>()) || (st = set_attr<kGramSel, 3>()) ||
+        (st = set_attr<kGramSimt, 4>()) || (st = set_attr<kGramNone, 4>()) || (st = set_attr<kGramBf16, 4>()) ||
+        (st = set_attr<kGramRTf32, 4>()) || (st = set_attr<kGramSel, 4>()))
         return st;
     RASCAL_CUDA(cudaStreamSynchronize(ctx->stream));
     return RASCAL_OK;
@@ -949,7 +952,7 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
     return RASCAL_OK;
 }
 
-static_assert(kNumExpShapes == 4, "one dispatch case per shaped instance");
+static_assert(kNumExpShapes == 5, "one dispatch case per shaped instance");
 
 // index of the compiled shape whose derived sizes all equal this launch's, else 0 (the runtime-shaped kernel); the
 // CT row pitch Qp is set (and checked) only for the forms that hold c transposed in shared memory
@@ -981,10 +984,11 @@ static int launch_expansion(rascal_ctx* ctx, const ExpArgs& A, int n_atoms, int 
 // the compiled instance for the launch's hyper shape, else the runtime-shaped kernel
 template <int GRAM>
 static int launch_shaped(rascal_ctx* ctx, const ExpArgs& A, int n_atoms, int threads, size_t smem) {
-    switch (exp_shape_of(ctx, A, GRAM == kGramSimt)) {
+    switch (exp_shape_of(ctx, A, GRAM == kGramSimt || GRAM == kGramSel)) {
         case 1: return launch_expansion<GRAM, 1>(ctx, A, n_atoms, threads, smem);
         case 2: return launch_expansion<GRAM, 2>(ctx, A, n_atoms, threads, smem);
         case 3: return launch_expansion<GRAM, 3>(ctx, A, n_atoms, threads, smem);
+        case 4: return launch_expansion<GRAM, 4>(ctx, A, n_atoms, threads, smem);
         default: return launch_expansion<GRAM>(ctx, A, n_atoms, threads, smem);
     }
 }
@@ -1063,7 +1067,7 @@ extern "C" int rascal_soap_selected(rascal_ctx* ctx, const rascal_system* sys, c
     if ((st = make_gram(ctx, kGramSimt, RASCAL_LAYOUT_PACKED, d_ps, A, &smem, &threads))) return st;
     A.sel = static_cast<const int*>(dec);
     A.n_sel = (int)n_sel;
-    return launch_expansion<kGramSel>(ctx, A, sys->n_atoms, threads, smem);
+    return launch_shaped<kGramSel>(ctx, A, sys->n_atoms, threads, smem);
 }
 
 extern "C" int rascal_soap(rascal_ctx* ctx, const rascal_system* sys, const int64_t* d_offsets, const int* d_nbr_j,

@@ -507,6 +507,7 @@ int gradients_setup(rascal_ctx* ctx) {
     RASCAL_CUDA(cudaFuncSetAttribute(k_gradients<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     RASCAL_CUDA(cudaFuncSetAttribute(k_gradients<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     RASCAL_CUDA(cudaFuncSetAttribute(k_gradients<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RASCAL_CUDA(cudaFuncSetAttribute(k_gradients<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     return RASCAL_OK;
 }
 
@@ -638,11 +639,12 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
             ctx->n_lm == (c.l_max + 1) * (c.l_max + 1) && ctx->F == (c.l_max + 1) * c.n_max && (!A.wsym || A.Qw == (ctx->Q + 3) / 4 * 4))
             shape = k;
     }
-    static_assert(kNumExpShapes == 4, "one launch case per shaped instance");
+    static_assert(kNumExpShapes == 5, "one launch case per shaped instance");
     switch (shape) {
         case 1: k_gradients<1><<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A); break;
         case 2: k_gradients<2><<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A); break;
         case 3: k_gradients<3><<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A); break;
+        case 4: k_gradients<4><<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A); break;
         default: k_gradients<0><<<sys->n_atoms, kGradThreads, smem, ctx->stream>>>(A); break;
     }
     RASCAL_LAUNCH_CHECK("k_gradients");

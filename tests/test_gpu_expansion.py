@@ -138,7 +138,7 @@ def test_fused_soap_equals_separate_calls(rg):
     assert np.max(np.abs(p1.cpu().numpy() - p2.cpu().numpy())) <= 1e-6 * np.max(np.abs(p1.cpu().numpy()))
 
 
-@pytest.mark.parametrize("hyp_name", ["HYPERS_BATCH", "HYPERS_LARGE", "HYPERS_DIFF"])
+@pytest.mark.parametrize("hyp_name", ["HYPERS_BATCH", "HYPERS_LARGE", "HYPERS_DIFF", "HYPERS_MLP"])
 def test_shaped_instances_match_oracle(rg, hyp_name):
     # the hyper shapes with their own compiled instance of the fused FP32 kernel (compile-time n_max, l_max and
     # species count): fused c and p, PACKED and FULL, against the oracle, with a crowded centre (more pairs than one
@@ -158,25 +158,43 @@ def test_shaped_instances_match_oracle(rg, hyp_name):
     ds = rg.DeviceSystem.from_numpy(s)
     pairs = calc.neighbours(ds)
     assert np.diff(pairs.offsets.cpu().numpy()).max() > 32
+    # at n_max = 16 (cond(S) = 5.7e10) the FP64 S^-1/2 of the GPU and of the oracle agree only to ~5e-7 relative
+    # (the oracle's own is pinned to 40 digits at that level); after the cancellation inside a crowded centre's
+    # (species) block this reaches 2.2e-5 of the block's max, identically with the exact per-pair radial path and
+    # with the runtime-shaped kernel, so the bar follows the basis transform there: 5e-5 for c, twice that for p
+    tol_c = TOL if h.n_max <= 12 else 5e-5
+    tol_p = TOL if h.n_max <= 12 else 1e-4
     for layout in ("packed", "full"):
         c, p = calc.soap(ds, pairs, layout=layout)
         p_sep = calc.power_spectrum(calc.spherical_expansion(ds, pairs), layout=layout)
         calc.sync()
         c, p, p_sep = c.cpu().numpy(), p.cpu().numpy(), p_sep.cpu().numpy()
         p_ref = osoap.power_spectrum(c_ref, h, layout).reshape(len(pos), h.l_max + 1, -1)
-        assert block_rel_err(c, c_ref, 2) <= TOL
-        assert block_rel_err(ps_blocks(p, h.l_max), p_ref, 2) <= TOL, layout
-        assert block_rel_err(ps_blocks(p_sep, h.l_max), p_ref, 2) <= TOL, layout
+        assert block_rel_err(c, c_ref, 2) <= tol_c
+        assert block_rel_err(ps_blocks(p, h.l_max), p_ref, 2) <= tol_p, layout
+        assert block_rel_err(ps_blocks(p_sep, h.l_max), p_ref, 2) <= tol_p, layout
         assert np.all(c[-1] == 0.0) and np.all(p[-1] == 0.0)
     # the tensor-core forms and the coefficients-only call have their own instances for these shapes
     c_only = calc.spherical_expansion(ds, pairs).cpu().numpy()
-    assert block_rel_err(c_only, c_ref, 2) <= TOL
+    assert block_rel_err(c_only, c_ref, 2) <= tol_c
     p_ref = osoap.power_spectrum(c_ref, h, "packed").reshape(len(pos), h.l_max + 1, -1)
     for prec, tol in (("tf32x3", TOL), ("bf16", 2.0 ** -7)):
-        c_tc, p_tc = calc.soap(ds, pairs, precision=prec)
-        calc.sync()
-        assert block_rel_err(c_tc.cpu().numpy(), c_ref, 2) <= TOL, prec
-        assert block_rel_err(ps_blocks(p_tc.cpu().numpy(), h.l_max), p_ref, 2) <= tol, prec
+        try:
+            c_tc, p_tc = calc.soap(ds, pairs, precision=prec)
+            calc.sync()
+        except rg.RascalError as e:  # TF32 hi/lo tiles of Q > 96 exceed shared memory: refused, not run
+            assert e.code == rg._lib.RASCAL_E_UNSUPPORTED and prec == "tf32x3" and h.q > 96
+            continue
+        assert block_rel_err(c_tc.cpu().numpy(), c_ref, 2) <= tol_c, prec
+        assert block_rel_err(ps_blocks(p_tc.cpu().numpy(), h.l_max), p_ref, 2) <= max(tol, tol_p), prec
+    # selected packed features (the selection form's instance for the same shape)
+    F = h.n_features("packed")
+    sel = np.random.default_rng(3).choice(F, size=F // 7, replace=False).astype(np.int32)
+    c_sel, p_sel = calc.soap_selected(ds, pairs, sel)
+    calc.sync()
+    assert np.array_equal(c_sel.cpu().numpy(), c_only)
+    ref_sel = osoap.power_spectrum(c_ref, h, "packed").reshape(len(pos), -1)[:, sel]
+    assert block_rel_err(p_sel.cpu().numpy(), ref_sel, 1) <= tol_p
     # forces and virial of the linear energy model through the gradient kernel's instance for the same shape
     import torch
 
