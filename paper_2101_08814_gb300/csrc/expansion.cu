@@ -216,6 +216,31 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
 
         for (int pos = 0; pos < seg_len; pos += chunk) {  // pair offsets relative to the centre's segment
             const int nc = min(chunk, seg_len - pos);
+            if (chunk <= 32) {
+                // warp 0 stages the chunk, one pair per lane, and lists it by species straight from its registers
+                if (warp == 0) {
+                    int a = -2;  // lanes without a pair match no species
+                    if (lane < nc) {
+                        const float4 v = seg_rij[pos + lane];
+                        const int j = seg_j[pos + lane];
+                        const int lab = A.species[j];
+                        a = (lab >= 0 && lab < 256) ? A.lut[lab] : -1;
+                        if (a < 0) atomicOr(A.flags, kFlagSpecies);
+                        if (!(v.w > 1e-6f)) a = -1;  // coincident atoms are flagged by the neighbour search
+                        s_vec[lane] = v;
+                        s_fc[lane] = cutoff_fp32(v.w, A.r_cut, A.width);
+                    }
+                    int base = 0;
+                    #pragma unroll 1
+                    for (int ga = 0; ga < na; ++ga) {
+                        if (lane == 0) s_start[ga] = base;
+                        const unsigned m = __ballot_sync(0xffffffffu, a == a0 + ga);
+                        if (a == a0 + ga) s_list[base + __popc(m & ((1u << lane) - 1u))] = lane;
+                        base += __popc(m);
+                    }
+                    if (lane == 0) s_start[na] = base;
+                }
+            } else {
             #pragma unroll 1
             for (int t = tid; t < nc; t += blockDim.x) {
                 const float4 v = seg_rij[pos + t];
@@ -245,6 +270,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     }
                 }
                 if (lane == 0) s_start[na] = base;
+            }
             }
             __syncthreads();
             const int n_list = s_start[na];
