@@ -190,20 +190,28 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
     // one 4 x 4 register tile of chat_l = Ws_l C_l (rows 4 qt.., columns 4 st.. of the l block), Ws_l dense and
     // symmetric with row pitch Qw (in global memory for the linear model, in shared memory for a per-centre dE/dp)
     auto adjoint_tile = [&](const float* Wl, const float* Cl, int Lq, int l, int qt, int st, bool w_global) {
-        float acc[4][4];
+        // paired FMAs (fma.rn.f32x2): each product rounded exactly as fmaf rounds it
+        uint64_t ap[4][2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+        for (int u = 0; u < 4; ++u) ap[u][0] = ap[u][1] = 0ull;
         for (int k = 0; k < kQ; ++k) {
             const float4 w4 = w_global ? __ldg(reinterpret_cast<const float4*>(Wl + k * kQw))
                                        : *reinterpret_cast<const float4*>(Wl + k * kQw);
             const float4 c4 = *reinterpret_cast<const float4*>(Cl + k * Lq);
-            const float ww[4] = {w4.x, w4.y, w4.z, w4.w}, cc[4] = {c4.x, c4.y, c4.z, c4.w};
+            const float ww[4] = {w4.x, w4.y, w4.z, w4.w};
+            const uint64_t c01 = f2_pack(c4.x, c4.y), c23 = f2_pack(c4.z, c4.w);
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t wu = f2_pack(ww[u], ww[u]);
+                ap[u][0] = f2_fma(wu, c01, ap[u][0]);
+                ap[u][1] = f2_fma(wu, c23, ap[u][1]);
+            }
+        }
+        float acc[4][4];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ww[u], cc[v], acc[u][v]);
+        for (int u = 0; u < 4; ++u) {
+            f2_unpack(ap[u][0], acc[u][0], acc[u][1]);
+            f2_unpack(ap[u][1], acc[u][2], acc[u][3]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
