@@ -95,6 +95,7 @@ __device__ inline int stage_shift(const float* dst) { return (int)((reinterpret_
 // Writes count floats staged at st (st and dst congruent mod 16 bytes) to dst: thread 0 issues one bulk copy for
 // the aligned body, threads 0..6 store the ragged head and tail. Call after the fence and barrier that publish st.
 __device__ inline void store_staged(float* dst, const float* st, int count) {
+    if (threadIdx.x >= 32) return;  // warp 0 does all of it: the other warps skip the address arithmetic
     const int head = min((4 - stage_shift(dst)) & 3, count);
     const int body = (count - head) & ~3;
     const int tail = count - head - body;
