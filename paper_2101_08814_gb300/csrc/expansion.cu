@@ -130,6 +130,8 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
     const int kNmax = SHAPE ? C.n_max : A.n_max, kLmax = SHAPE ? C.l_max : A.l_max, kS = SHAPE ? C.S : A.S;
     const int kQ = SHAPE ? C.n_max * C.S : A.Q, kNlm = SHAPE ? (C.l_max + 1) * (C.l_max + 1) : A.n_lm;
     const int kNpad = SHAPE ? exp_npad(C.n_max) : A.n_pad, kFpad = SHAPE ? (C.l_max + 1) * exp_npad(C.n_max) : A.F_pad;
+    // with n_max a multiple of 4 the padded radial slot f = l n_pad + n is the table column l n_max + n itself
+    constexpr bool kFmapId = SHAPE != 0 && C.n_max % 4 == 0;
     const int kF = SHAPE ? (C.l_max + 1) * C.n_max : A.F, kLy = SHAPE ? exp_ly(C.l_max) : A.Ly;
     const int kQp = SHAPE ? exp_qp(C.n_max * C.S) : A.Qp, kTs = SHAPE ? exp_ts(C.n_max, C.l_max) : A.T_s;
     const int kWs = SHAPE ? (exp_ts(C.n_max, C.l_max) + 31) / 32 : A.W_s;
@@ -155,8 +157,10 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
 
     const int i = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    #pragma unroll 1
-    for (int t = tid; t < kFpad; t += blockDim.x) s_fmap[t] = A.fmap[t];
+    if (!kFmapId) {
+        #pragma unroll 1
+        for (int t = tid; t < kFpad; t += blockDim.x) s_fmap[t] = A.fmap[t];
+    }
     constexpr bool kCT = (GRAM == kGramSimt || GRAM == kGramSel);  // c held transposed in shared memory
     if (kCT) {  // columns Q..ceil4(Q)-1 of CT are read by the edge tiles and must be zero
         float* CT = reinterpret_cast<float*>(gram);
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 if (A.pre_G) {  // per-pair values (EXACT / MLP radial modes)
                     const float* prow = seg_G + (pos + p) * kF;
                     for (int fp = lane; fp < kFpad; fp += 32) {
-                        const int col = s_fmap[fp];
+                        const int col = kFmapId ? fp : s_fmap[fp];
                         grow[fp] = col >= 0 ? fc * __ldg(prow + col) : 0.0f;
                     }
                 } else {        // cubic spline: interval k, local coordinate u in [0, 1)
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     const float u = x - (float)k;
                     const float4* trow = A.table + k * kF;
                     for (int fp = lane; fp < kFpad; fp += 32) {
-                        const int col = s_fmap[fp];
+                        const int col = kFmapId ? fp : s_fmap[fp];
                         const float4 c = col >= 0 ? __ldg(trow + col) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                         grow[fp] = fc * fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x);
                     }

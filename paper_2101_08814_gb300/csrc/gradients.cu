@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
     const int kNmax = SHAPE ? Cs.n_max : A.n_max, kLmax = SHAPE ? Cs.l_max : A.l_max;
     const int kQ = SHAPE ? Cs.n_max * Cs.S : A.Q, kNlm = SHAPE ? (Cs.l_max + 1) * (Cs.l_max + 1) : A.n_lm;
     const int kNpad = SHAPE ? exp_npad(Cs.n_max) : A.n_pad, kFpad = SHAPE ? (Cs.l_max + 1) * exp_npad(Cs.n_max) : A.F_pad;
+    // with n_max a multiple of 4 the padded radial slot f = l n_pad + n is the table column l n_max + n itself
+    constexpr bool kFmapId = SHAPE != 0 && Cs.n_max % 4 == 0;
     const int kF = SHAPE ? (Cs.l_max + 1) * Cs.n_max : A.F, kQw = SHAPE ? (Cs.n_max * Cs.S + 3) / 4 * 4 : A.Qw;
     const int kLpAdj = SHAPE ? exp_lp(Cs.l_max + 1) : A.Lp_adj;
     const int kAdjTasks = SHAPE ? (Cs.n_max * Cs.S + 3) / 4 * (exp_lp(Cs.l_max + 1) / 4) : A.n_adj_tasks;
@@ -181,7 +183,8 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int L1 = kLmax + 1;
     for (int lm = tid; lm < kNlm; lm += blockDim.x) s_lofm[lm] = (int)sqrtf((float)lm);  // l with l^2 <= lm
-    for (int t = tid; t < kFpad; t += blockDim.x) s_fmap[t] = A.fmap[t];
+    if (!kFmapId)
+        for (int t = tid; t < kFpad; t += blockDim.x) s_fmap[t] = A.fmap[t];
     const int lab_i = A.species[i];
     const int a_i = (lab_i >= 0 && lab_i < 256) ? A.lut[lab_i] : -1;
     const float* Gp = A.grad_ps ? A.grad_ps + (int64_t)i * A.Fp : (a_i >= 0 ? A.weights + (int64_t)a_i * A.Fp : nullptr);
@@ -341,7 +344,7 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
                 const float* pg = A.pre_G + (pos + p) * kF;
                 const float* pd = A.pre_D + (pos + p) * kF;
                 for (int fp = lane; fp < kFpad; fp += 32) {
-                    const int col = s_fmap[fp];
+                    const int col = kFmapId ? fp : s_fmap[fp];
                     const float g = col >= 0 ? __ldg(pg + col) : 0.0f, dg = col >= 0 ? __ldg(pd + col) : 0.0f;
                     gd[fp] = make_float2(f * g, df * g + f * dg);
                 }
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
                 const float u = x - (float)k;
                 const float4* trow = A.table + k * kF;
                 for (int fp = lane; fp < kFpad; fp += 32) {
-                    const int col = s_fmap[fp];
+                    const int col = kFmapId ? fp : s_fmap[fp];
                     const float4 cf = col >= 0 ? __ldg(trow + col) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     const float g = fmaf(u, fmaf(u, fmaf(u, cf.w, cf.z), cf.y), cf.x);
                     const float dg = fmaf(u, fmaf(u, 3.0f * cf.w, 2.0f * cf.z), cf.y) * A.inv_delta;
