@@ -619,26 +619,30 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
     // the largest chunk (<= 32: warp 0 runs the per-pair phase) that keeps five CTAs per SM (48 registers); a
     // per-centre dE/dp takes the tiled adjoint with one dense l block in shared memory when four CTAs per SM keep a
     // chunk of at least 8 pairs, else the per-element adjoint
-    A.w_tiled = 0;
-    A.w_off = 0;
     int chunk = 32;
+    bool w_tiled = false;
     if (!d_weights) {
         while (chunk > 8 && grad_smem(ctx, chunk, true, true) > 54 * 1024) --chunk;
-        if (grad_smem(ctx, chunk, true, true) <= 54 * 1024) {
-            A.w_tiled = 1;
-            A.Qw = Qw;
-            A.Lp_adj = P.Lp;
-            A.w_off = (int)grad_w_off(ctx, chunk);
-        } else {
-            chunk = 32;
-        }
+        w_tiled = grad_smem(ctx, chunk, true, true) <= 54 * 1024;
+        if (!w_tiled) chunk = 32;
     }
-    const bool tiled = A.wsym != nullptr || A.w_tiled;
-    if (!A.w_tiled)
+    const bool tiled = A.wsym != nullptr || w_tiled;
+    if (!w_tiled)
         while (chunk > 1 && grad_smem(ctx, chunk, tiled) > 44 * 1024) --chunk;
+    // the radial and contraction phases deal the chunk's pairs to the 8 warps: a multiple of 8 leaves no nearly
+    // empty second round (rounding down only shrinks the shared memory below)
+    if (chunk > kGradThreads / 32) chunk = chunk / (kGradThreads / 32) * (kGradThreads / 32);
+    // every shared-memory offset and the size come from this final chunk
     A.chunk = chunk;
+    A.w_tiled = w_tiled ? 1 : 0;
+    A.w_off = 0;
+    if (w_tiled) {
+        A.Qw = Qw;
+        A.Lp_adj = P.Lp;
+        A.w_off = (int)grad_w_off(ctx, chunk);
+    }
     A.aux_off = (int)grad_aux_off(ctx, chunk, tiled);
-    const size_t smem = grad_smem(ctx, chunk, tiled, A.w_tiled != 0);
+    const size_t smem = grad_smem(ctx, chunk, tiled, w_tiled);
     if (smem > 220 * 1024) return set_error(RASCAL_E_UNSUPPORTED, "hypers too large for the gradient kernel");
     if ((st = radial_precompute(ctx, sys, d_offsets, d_rij, true, &A.pre_G, &A.pre_D))) return st;
     // a compiled instance for the hyper shape when the plan's sizes match it (kExpShapes), else the generic kernel
