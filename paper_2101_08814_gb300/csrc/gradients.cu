@@ -362,12 +362,14 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
                 }
             }
         }
-        // Y and dY/du (gradient of the polynomial extension), forward mode through the recurrence: warp w runs the
-        // m = w chains, lanes over pairs
-        for (int m = warp; m < L1; m += nwarps) {
+        // Y and dY/du (gradient of the polynomial extension), forward mode through the recurrence: lanes over the
+        // chunk's pairs, one chain of m per lane; a chunk of at most 8 pairs gives each warp four values of m (8 lanes
+        // each), a larger one gives warp w the m = w, w + nwarps, ... chains on all 32 lanes
+        const int lpm = nc <= 8 ? 8 : 32, mpw = 32 / lpm;
+        for (int m = warp * mpw + lane / lpm; m < L1; m += nwarps * mpw) {
             const float km = c_ylm_K[m], fm = (float)m;
 #pragma unroll 1
-            for (int p = lane; p < nc; p += 32) {
+            for (int p = lane % lpm; p < nc; p += lpm) {
                 const float4 v = s_vec[p];
                 const float inv_r = v.w > 1e-6f ? 1.0f / v.w : 0.0f;
                 const float x = v.x * inv_r, y = v.y * inv_r, z = v.z * inv_r;
