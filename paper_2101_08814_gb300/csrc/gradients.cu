@@ -363,9 +363,9 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
             }
         }
         // Y and dY/du (gradient of the polynomial extension), forward mode through the recurrence: lanes over the
-        // chunk's pairs, one chain of m per lane; a chunk of at most 8 pairs gives each warp four values of m (8 lanes
-        // each), a larger one gives warp w the m = w, w + nwarps, ... chains on all 32 lanes
-        const int lpm = nc <= 8 ? 8 : 32, mpw = 32 / lpm;
+        // chunk's pairs, one chain of m per lane; a chunk of at most 8 (16) pairs gives each warp four (two) values
+        // of m on 8 (16) lanes each, a larger one gives warp w the m = w, w + nwarps, ... chains on all 32 lanes
+        const int lpm = nc <= 8 ? 8 : (nc <= 16 ? 16 : 32), mpw = 32 / lpm;
         for (int m = warp * mpw + lane / lpm; m < L1; m += nwarps * mpw) {
             const float km = c_ylm_K[m], fm = (float)m;
 #pragma unroll 1
@@ -631,9 +631,11 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
     const bool tiled = A.wsym != nullptr || w_tiled;
     if (!w_tiled)
         while (chunk > 1 && grad_smem(ctx, chunk, tiled) > 44 * 1024) --chunk;
-    // the radial and contraction phases deal the chunk's pairs to the 8 warps: a multiple of 8 leaves no nearly
-    // empty second round (rounding down only shrinks the shared memory below)
-    if (chunk > kGradThreads / 32) chunk = chunk / (kGradThreads / 32) * (kGradThreads / 32);
+    // the radial and contraction phases deal the chunk's pairs to the 8 warps: a chunk one or two pairs past a
+    // multiple of 8 is rounded down, so that no nearly empty last round remains (rounding down only shrinks the
+    // shared memory below)
+    constexpr int kW = kGradThreads / 32;
+    if (chunk > kW && chunk % kW <= 2) chunk -= chunk % kW;
     // every shared-memory offset and the size come from this final chunk
     A.chunk = chunk;
     A.w_tiled = w_tiled ? 1 : 0;
