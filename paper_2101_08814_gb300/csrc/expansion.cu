@@ -615,29 +615,35 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         // groups of l alternate between two staging halves; each half is written again only after the bulk store
         // issued from it two groups earlier has finished reading it
         for (int gi = 0; gi < A.n_groups; ++gi) {
-            const int lo = A.g_lo[gi];
-            float* dst = pout + (int64_t)lo * A.per_l;
-            float* st = stage + (gi & 1) * A.p_half + stage_shift(dst);
             if (gi >= 2) {
                 if (tid == 0) bulk_wait_read<1>();
                 __syncthreads();
             }
             // tasks are sorted by decreasing cost (l); alternate rounds are dealt in reverse thread order so that
-            // the threads with the longest first tile get the shortest second one
-            const int T = blockDim.x;
-            for (int r = 0; A.g_tbeg[gi] + r * T < A.g_tend[gi]; ++r) {
-                const int t = A.g_tbeg[gi] + r * T + ((r & 1) ? T - 1 - tid : tid);
-                if (t >= A.g_tend[gi]) continue;
+            // the threads with the longest first tile get the shortest second one. Only the threads that stage
+            // tiles work out the staging address and fence their writes for the bulk copy.
+            const int T = blockDim.x, tbeg = A.g_tbeg[gi], tend = A.g_tend[gi];
+            bool wrote = false;
+            for (int r = 0; tbeg + r * T < tend; ++r) {
+                const int t = tbeg + r * T + ((r & 1) ? T - 1 - tid : tid);
+                if (t >= tend) continue;
+                const int lo = A.g_lo[gi];
+                float* st = stage + (gi & 1) * A.p_half + stage_shift(pout + (int64_t)lo * A.per_l);
                 const int packed = __ldg(&A.ps_tasks[t]);
                 const int l = packed & 0xff, t1 = (packed >> 8) & 0xff, t2 = (packed >> 16) & 0xff;
                 float acc[4][4];
                 gram_tile_fp32(CT, kQp, l, t1, t2, acc);
                 store_tile_fp32(st + (l - lo) * A.per_l, kQ, A.layout, t1, t2,
                                 A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f, acc);
+                wrote = true;
             }
-            fence_proxy_async_smem();
+            if (wrote) fence_proxy_async_smem();
             __syncthreads();
-            store_staged(dst, st, (A.g_hi[gi] - lo) * A.per_l);
+            if (warp == 0) {
+                const int lo = A.g_lo[gi];
+                float* dst = pout + (int64_t)lo * A.per_l;
+                store_staged(dst, stage + (gi & 1) * A.p_half + stage_shift(dst), (A.g_hi[gi] - lo) * A.per_l);
+            }
         }
         if (tid == 0) bulk_wait_all();
         return;
