@@ -23,6 +23,20 @@
 
 namespace rascal {
 
+// Structure of atom i: the largest s < n_s with offs[s] <= i (offsets non-decreasing, offs[n_s] = the atom count),
+// found by one warp in rounds of 32 probes (two rounds for up to 1024 structures); every lane returns it.
+__device__ inline int warp_find_structure(const int* __restrict__ offs, int n_s, int i, int lane) {
+    int lo = 0, hi = n_s;  // offs[lo] <= i < offs[hi]
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int idx = lo + lane * step;
+        const unsigned m = __ballot_sync(0xffffffffu, idx < hi && offs[idx] <= i);  // a prefix of the lanes
+        lo += (31 - __clz(m)) * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
 // E_s = sum_{i in s} w_{a_i} . p_i, one CTA per centre, FP32 partial sums, FP64 across warps and one atomic per centre.
 __global__ void k_linear_energy(int N, int n_s, const int* __restrict__ offs, const int* __restrict__ species,
                                 const int* __restrict__ lut, const float* __restrict__ ps, const float* __restrict__ w,
@@ -30,14 +44,7 @@ __global__ void k_linear_energy(int N, int n_s, const int* __restrict__ offs, co
     __shared__ double red[32];
     const int i = blockIdx.x;
     int sid = 0;
-    if (threadIdx.x == 0) {  // structure of centre i, looked up first so that its latency overlaps the sum
-        int hi = n_s;
-        while (hi - sid > 1) {
-            const int mid = (sid + hi) >> 1;
-            if (offs[mid] <= i) sid = mid;
-            else hi = mid;
-        }
-    }
+    if (threadIdx.x < 32) sid = warp_find_structure(offs, n_s, i, threadIdx.x);  // read by thread 0 at the end
     const int lab = species[i];
     const int a = (lab >= 0 && lab < 256) ? lut[lab] : -1;
     // FP32 partial sums per thread and warp (GB300's FP64 rate is a small fraction of its FP32 rate), FP64 across
@@ -171,14 +178,9 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
     __shared__ int s_sid;
 
     const int i = blockIdx.x;
-    if (threadIdx.x == 0) {  // structure of centre i, looked up early so that its latency overlaps the prologue
-        int lo = 0, hi = A.n_s;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (A.offs[mid] <= i) lo = mid;
-            else hi = mid;
-        }
-        s_sid = lo;
+    if ((threadIdx.x >> 5) == (blockDim.x >> 5) - 1) {  // the last warp is idle while warp 0 stages the pairs
+        const int sid = warp_find_structure(A.offs, A.n_s, i, threadIdx.x & 31);
+        if ((threadIdx.x & 31) == 0) s_sid = sid;
     }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int L1 = kLmax + 1;
