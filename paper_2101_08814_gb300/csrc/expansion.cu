@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 float* grow = s_G + q * kFpad;
                 if (A.pre_G) {  // per-pair values (EXACT / MLP radial modes)
                     const float* prow = seg_G + (pos + p) * kF;
+                    #pragma unroll
                     for (int fp = lane; fp < kFpad; fp += 32) {
                         const int col = kFmapId ? fp : s_fmap[fp];
                         grow[fp] = col >= 0 ? fc * __ldg(prow + col) : 0.0f;
@@ -339,6 +340,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     const int k = min(max((int)x, 0), A.M - 1);
                     const float u = x - (float)k;
                     const float4* trow = A.table + k * kF;
+                    #pragma unroll
                     for (int fp = lane; fp < kFpad; fp += 32) {
                         const int col = kFmapId ? fp : s_fmap[fp];
                         const float4 c = col >= 0 ? __ldg(trow + col) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
