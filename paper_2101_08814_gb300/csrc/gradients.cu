@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
             if (A.pre_G) {
                 const float* pg = A.pre_G + (pos + p) * kF;
                 const float* pd = A.pre_D + (pos + p) * kF;
+                #pragma unroll
                 for (int fp = lane; fp < kFpad; fp += 32) {
                     const int col = kFmapId ? fp : s_fmap[fp];
                     const float g = col >= 0 ? __ldg(pg + col) : 0.0f, dg = col >= 0 ? __ldg(pd + col) : 0.0f;
@@ -355,6 +356,7 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
                 const int k = min(max((int)x, 0), A.M - 1);
                 const float u = x - (float)k;
                 const float4* trow = A.table + k * kF;
+                #pragma unroll
                 for (int fp = lane; fp < kFpad; fp += 32) {
                     const int col = kFmapId ? fp : s_fmap[fp];
                     const float4 cf = col >= 0 ? __ldg(trow + col) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
