@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
         my_nt = (packed >> 8) & 0xff;
         my_mt = (packed >> 16) & 0xff;
     }
-    __syncthreads();
+    // the SIMT Gram modes read what the prologue wrote (fmap, CT padding) only after the barriers of the pair phase
+    // or of the CT hand-off; the tensor-core modes need it here (tile zeroing before given operands, TMEM address)
+    if (!kCT) __syncthreads();
     const int g_off = my_l * kNpad + 4 * my_nt;   // offset inside a G row
     const int y_off = exp_lp(my_l) + 4 * my_mt;       // offset inside a Y row
 
@@ -615,12 +617,10 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
             return;
         }
         // groups of l alternate between two staging halves; each half is written again only after the bulk store
-        // issued from it two groups earlier has finished reading it
+        // issued from it two groups earlier has finished reading it. Thread 0, which issues the stores, waits for
+        // the previous group's store to have read its half before the barrier that ends a group, so that one
+        // barrier per group serves both hand-offs.
         for (int gi = 0; gi < A.n_groups; ++gi) {
-            if (gi >= 2) {
-                if (tid == 0) bulk_wait_read<1>();
-                __syncthreads();
-            }
             // tasks are sorted by decreasing cost (l); alternate rounds are dealt in reverse thread order so that
             // the threads with the longest first tile get the shortest second one. Only the threads that stage
             // tiles work out the staging address and fence their writes for the bulk copy.
@@ -640,6 +640,7 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                 wrote = true;
             }
             if (wrote) fence_proxy_async_smem();
+            if (tid == 0 && gi >= 1) bulk_wait_read<0>();  // the store of gi - 1 is done with the half of gi + 1
             __syncthreads();
             if (warp == 0) {
                 const int lo = A.g_lo[gi];
