@@ -366,7 +366,9 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     }
                 }
             }
-            __syncthreads();
+            // the next chunk or round restages the pair buffers; after the last one the SIMT Gram modes write only
+            // CT, and the barrier that hands CT over comes before anything reuses the pair buffers
+            if (!kCT || pos + chunk < seg_len || round + 1 < kRounds) __syncthreads();
         }
         float acc[4][4];
 #pragma unroll

@@ -164,14 +164,15 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
     float* s_H = reinterpret_cast<float*>(smem_raw);          // chat [Q][n_lm]
     // the coefficients are needed only by the adjoint, before the pair loop: they share the pair area
     float* s_C = s_H + QN4;                                   // [Q][n_lm], or [Q][Lp_adj] padded per l (tiled adjoint)
-    float4* s_vec = reinterpret_cast<float4*>(s_H + QN4);     // [chunk]
-    float4* s_Yv = s_vec + chunk;                             // [chunk][Yp]  (Y, dY/dux, dY/duy, dY/duz)
-    float4* s_acc = s_Yv + (size_t)chunk * Yp;                // [chunk]      (s, wx, wy, wz)
-    float2* s_GD = reinterpret_cast<float2*>(s_acc + chunk);  // [chunk][F_pad]  (f I, (f I)')
-    float* s_fc = reinterpret_cast<float*>(s_GD + (size_t)chunk * kFpad);
-    float* s_dfc = s_fc + chunk;
-    int* s_spc = reinterpret_cast<int*>(s_dfc + chunk);
-    int* s_j = s_spc + chunk;
+    // per-pair records (r_ji, f_cut, f_cut', species index, j): two buffers that alternate between chunks, so that
+    // the next chunk is staged while the current one is processed
+    float4* s_vec = reinterpret_cast<float4*>(s_H + QN4);     // [2][chunk]
+    float4* s_Yv = s_vec + 2 * chunk;                         // [chunk][Yp]  (Y, dY/dux, dY/duy, dY/duz)
+    float2* s_GD = reinterpret_cast<float2*>(s_Yv + (size_t)chunk * Yp);  // [chunk][F_pad]  (f I, (f I)')
+    float* s_fc = reinterpret_cast<float*>(s_GD + (size_t)chunk * kFpad);  // [2][chunk]
+    float* s_dfc = s_fc + 2 * chunk;                          // [2][chunk]
+    int* s_spc = reinterpret_cast<int*>(s_dfc + 2 * chunk);   // [2][chunk]
+    int* s_j = s_spc + 2 * chunk;                             // [2][chunk]
     int* s_lofm = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(s_vec) + A.aux_off);  // [n_lm] l of lm
     int* s_fmap = s_lofm + kNlm;                            // [F_pad]
     __shared__ double red[kGradThreads / 32][12];
@@ -304,22 +305,22 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
         s_H[e] = (A.ps_norm ? rsqrtf((float)(2 * l + 1)) : 1.0f) * acc;
     }
     }
-    // FP32 per-thread and per-warp sums (GB300's FP64 rate is a small fraction of its FP32 rate); FP64 across warps
-    float fi[3] = {0.0f, 0.0f, 0.0f};
-    float vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // per-lane sums of F_i (lanes 0..2) and of the virial (lanes 3..11, row-major): FP32 within a warp, FP64 across
+    // the warps (GB300's FP64 rate is a small fraction of its FP32 rate)
+    float racc = 0.0f;
     const int64_t seg_beg = A.offsets[i], seg_end = A.offsets[i + 1];
-    // the next chunk's r_ji and j are loaded into registers while the current chunk is processed
+    // the last warp stages the pairs (chunk <= 32: one pair per lane), with the next chunk's r_ji and j loaded into
+    // registers one chunk ahead
+    const bool stager = warp == nwarps - 1;
     float4 nv = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
     int nj = 0;
-    if (tid < chunk && seg_beg + tid < seg_end) {
-        nv = A.rij[seg_beg + tid];
-        nj = A.nbr_j[seg_beg + tid];
+    if (stager && lane < chunk && seg_beg + lane < seg_end) {
+        nv = A.rij[seg_beg + lane];
+        nj = A.nbr_j[seg_beg + lane];
     }
-    for (int64_t pos = seg_beg; pos < seg_end; pos += chunk) {
-        const int nc = (int)((seg_end - pos) < (int64_t)chunk ? (seg_end - pos) : (int64_t)chunk);
-        __syncthreads();
-        if (tid < nc) {
-            const int t = tid;
+    auto stage = [&](int64_t pos, int b) {  // the chunk at pos into record buffer b
+        const int t = lane;
+        if (t < chunk && pos + t < seg_end) {
             const float4 v = nv;
             const int j = nj;
             if (pos + chunk + t < seg_end) {
@@ -329,18 +330,27 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
             const int lab = A.species[j];
             int a = (lab >= 0 && lab < 256) ? A.lut[lab] : -1;
             if (!(v.w > 1e-6f)) a = -1;
-            s_vec[t] = v;
-            s_spc[t] = a;
-            s_j[t] = j;
+            const int o = b * chunk + t;
+            s_vec[o] = v;
+            s_spc[o] = a;
+            s_j[o] = j;
             float f, df;
             cutoff_and_slope(v.w, A.r_cut, A.width, f, df);
-            s_fc[t] = f;
-            s_dfc[t] = df;
+            s_fc[o] = f;
+            s_dfc[o] = df;
         }
+    };
+    __syncthreads();  // the adjoint is done with the staged coefficients, which share the pair area
+    if (stager) stage(seg_beg, 0);
+    int b = 0;
+    for (int64_t pos = seg_beg; pos < seg_end; pos += chunk, b ^= 1) {
+        const int nc = (int)((seg_end - pos) < (int64_t)chunk ? (seg_end - pos) : (int64_t)chunk);
+        // the chunk's records are staged, and the previous chunk's contraction is done with s_GD and s_Yv
         __syncthreads();
+        const int bo = b * chunk;  // this chunk's records: s_vec[bo + p], ...
         // radial values and slopes: one warp per pair, lanes over padded (l, n); the warps without a Y chain first
         for (int p = nwarps - 1 - warp; p < nc; p += nwarps) {
-            const float f = s_fc[p], df = s_dfc[p];
+            const float f = s_fc[bo + p], df = s_dfc[bo + p];
             float2* gd = s_GD + p * kFpad;
             if (A.pre_G) {
                 const float* pg = A.pre_G + (pos + p) * kF;
@@ -352,7 +362,7 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
                     gd[fp] = make_float2(f * g, df * g + f * dg);
                 }
             } else {
-                const float x = s_vec[p].w * A.inv_delta;
+                const float x = s_vec[bo + p].w * A.inv_delta;
                 const int k = min(max((int)x, 0), A.M - 1);
                 const float u = x - (float)k;
                 const float4* trow = A.table + k * kF;
@@ -374,7 +384,7 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
             const float km = c_ylm_K[m], fm = (float)m;
 #pragma unroll 1
             for (int p = lane % lpm; p < nc; p += lpm) {
-                const float4 v = s_vec[p];
+                const float4 v = s_vec[bo + p];
                 const float inv_r = v.w > 1e-6f ? 1.0f / v.w : 0.0f;
                 const float x = v.x * inv_r, y = v.y * inv_r, z = v.z * inv_r;
                 float cm = 1.0f, sm = 0.0f, cm1 = 0.0f, sm1 = 0.0f;  // (x+iy)^m and (x+iy)^(m-1)
@@ -410,10 +420,12 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
                 }
             }
         }
+        // the next chunk's records go to the other buffer, whose last readers finished before this chunk's barrier
+        if (stager && pos + chunk < seg_end) stage(pos + chunk, b ^ 1);
         __syncthreads();
-        // contraction with chat: one warp per pair, lanes over lm
+        // contraction with chat, then dE/dr_ji, the force scatter and the virial: one warp per pair, lanes over lm
         for (int p = warp; p < nc; p += nwarps) {
-            const int a = s_spc[p];
+            const int a = s_spc[bo + p];
             if (a < 0) continue;  // warp-uniform
             const float* H = s_H + a * kNmax * n_lm;
             const float2* gd = s_GD + p * kFpad;
@@ -442,45 +454,32 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
                 Wy += __shfl_xor_sync(0xffffffffu, Wy, o);
                 Wz += __shfl_xor_sync(0xffffffffu, Wz, o);
             }
-            if (lane == 0) s_acc[p] = make_float4(S, Wx, Wy, Wz);
-        }
-        __syncthreads();
-        // per pair: dE/dr_ji, force scatter, virial
-        for (int p = tid; p < nc; p += blockDim.x) {
-            if (s_spc[p] < 0) continue;
-            const float4 v = s_vec[p];
+            const float4 v = s_vec[bo + p];
             const float inv_r = 1.0f / v.w;
             const float ux = v.x * inv_r, uy = v.y * inv_r, uz = v.z * inv_r;
-            const float4 acc = s_acc[p];
-            const float S = acc.x, Wx = acc.y, Wy = acc.z, Wz = acc.w;
             const float wu = Wx * ux + Wy * uy + Wz * uz;
-            const float g[3] = {S * ux + (Wx - wu * ux) * inv_r, S * uy + (Wy - wu * uy) * inv_r,
-                                S * uz + (Wz - wu * uz) * inv_r};
-            const float rv[3] = {v.x, v.y, v.z};
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) vir[3 * a + b] = fmaf(g[a], rv[b], vir[3 * a + b]);
-            const int j = s_j[p];
-            if (j != i) {
-                for (int a = 0; a < 3; ++a) {
-                    atomicAdd(&A.forces[3 * (int64_t)j + a], -g[a]);
-                    fi[a] += g[a];
+            const float g0 = S * ux + (Wx - wu * ux) * inv_r, g1 = S * uy + (Wy - wu * uy) * inv_r,
+                        g2 = S * uz + (Wz - wu * uz) * inv_r;
+            const int ra = lane < 3 ? lane : (lane - 3) / 3;  // lane 3 + 3 ra + rb: virial entry (ra, rb)
+            const float ga = ra == 0 ? g0 : (ra == 1 ? g1 : g2);
+            if (lane < 3) {
+                const int j = s_j[bo + p];
+                if (j != i) {
+                    atomicAdd(&A.forces[3 * (int64_t)j + lane], -ga);
+                    racc += ga;
                 }
+            } else if (lane < 12) {
+                const int rb = (lane - 3) - 3 * ra;
+                racc = fmaf(ga, rb == 0 ? v.x : (rb == 1 ? v.y : v.z), racc);
             }
         }
     }
     // block reduction of F_i and the virial
-    // the per-pair phase runs on threads < chunk <= 32, so warp 0 holds all the partial sums
-    if (warp == 0) {
-        float vals[12] = {fi[0], fi[1], fi[2], vir[0], vir[1], vir[2], vir[3], vir[4], vir[5], vir[6], vir[7], vir[8]};
-#pragma unroll
-        for (int k = 0; k < 12; ++k)
-            for (int o = 16; o > 0; o >>= 1) vals[k] += __shfl_xor_sync(0xffffffffu, vals[k], o);
-        if (lane == 0)
-            for (int k = 0; k < 12; ++k) red[0][k] = (double)vals[k];
-    }
+    if (lane < 12) red[warp][lane] = (double)racc;
     __syncthreads();
     if (tid < 12) {
-        const double s = red[0][tid];
+        double s = 0.0;
+        for (int w = 0; w < nwarps; ++w) s += red[w][tid];
         if (tid < 3) {
             if (s != 0.0) atomicAdd(&A.forces[3 * (int64_t)i + tid], (float)s);
         } else {
@@ -500,8 +499,8 @@ static size_t grad_aux_off(const rascal_ctx* ctx, int chunk, bool tiled) {
     const size_t QN4 = ((size_t)ctx->Q * ctx->n_lm + 3) / 4 * 4;
     const size_t QL4 = tiled ? ((size_t)ctx->Q * P.Lp + 3) / 4 * 4 : QN4;
     const size_t Yp = (size_t)(ctx->n_lm | 1);
-    const size_t pair_area = sizeof(float4) * chunk * (1 + Yp + 1) + sizeof(float2) * chunk * P.F_pad +
-                             sizeof(float) * 2 * chunk + sizeof(int) * 2 * chunk;
+    const size_t pair_area = sizeof(float4) * chunk * (2 + Yp) + sizeof(float2) * chunk * P.F_pad +
+                             2 * (sizeof(float) * 2 + sizeof(int) * 2) * chunk;  // two buffers of pair records
     return align_up(std::max(pair_area, sizeof(float) * QL4), 16);
 }
 
