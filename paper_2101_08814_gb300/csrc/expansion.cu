@@ -913,19 +913,39 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
         A.Qp = ((Q + 3) / 4 | 1) * 4;
         gram_bytes = sizeof(float) * (size_t)ctx->n_lm * A.Qp;
         A.ps_tasks = ctx->d_pstasks;
-        // staging: two halves that alternate between groups of l, so that the bulk store of one group overlaps
-        // the tiles of the next; a staged block may start up to 3 floats late (alignment with its target in
-        // global memory). (Staging the whole centre at once needs three CTAs per SM and measured slower.)
-        const size_t half = std::max((pair_region / 2) / 4 * 4, ((size_t)A.per_l + 3 + 3) / 4 * 4);
+        // staging: two halves that alternate between groups of consecutive l (descending, the task order), so that
+        // the bulk store of one group overlaps the tiles of the next; a staged block may start up to 3 floats late
+        // (alignment with its target in global memory). The halves may differ in size: of the splits of the pair
+        // region, the one that needs the fewest groups (fewest barriers and bulk stores) is taken, the more even one
+        // on a tie. (Staging the whole centre at once needs three CTAs per SM and measured slower.)
+        const size_t blk = (size_t)A.per_l;
+        auto half_for = [&](int n) { return ((size_t)n * blk + 3 + 3) / 4 * 4; };  // >= n blocks + 3 floats
+        auto groups_for = [&](int n0, int n1) {
+            int g = 0;
+            for (int left = L1; left > 0; ++g) left -= (g & 1) ? n1 : n0;
+            return g;
+        };
+        int n0 = 1, n1 = 1, n_g = groups_for(1, 1);  // one block per half (the region grows if that does not fit)
+        for (int a = 1; a <= L1; ++a) {
+            const size_t ha = half_for(a);
+            if (ha > pair_region) break;
+            const size_t rest = (pair_region - ha) / 4 * 4;
+            const int b = rest > 3 ? (int)std::min<size_t>((rest - 3) / blk, (size_t)L1) : 0;
+            if (a < L1 && b < 1) continue;
+            const int ng = groups_for(a, a < L1 ? b : 0);
+            if (ng < n_g || (ng == n_g && std::max(a, b) < std::max(n0, n1))) {
+                n0 = a;
+                n1 = a < L1 ? b : 0;
+                n_g = ng;
+            }
+        }
+        const size_t half = half_for(n0);
         A.p_half = (int)half;
-        // groups of consecutive l (descending, the task order) whose blocks fit one half
         const int Q4 = (Q + 3) / 4;
         const int per_tile_l = Q4 * (Q4 + 1) / 2;
-        const size_t cap = half - 3;
         int g = 0, t = 0, l = ctx->l_max;
         while (l >= 0) {
-            int n = 0;
-            while (l - n >= 0 && (size_t)(n + 1) * A.per_l <= cap) ++n;
+            const int n = std::min((g & 1) ? n1 : n0, l + 1);
             A.g_hi[g] = l + 1;
             A.g_lo[g] = l - n + 1;
             A.g_tbeg[g] = t;
@@ -935,7 +955,7 @@ static int make_gram(rascal_ctx* ctx, int mode, int layout, float* d_ps, ExpArgs
             ++g;
         }
         A.n_groups = g;
-        stage_need = 2 * half;
+        stage_need = half + (n1 > 0 ? (size_t)n1 * blk + 3 : 0);
     } else {
         if (Q > 128) return set_error(RASCAL_E_UNSUPPORTED, "tensor-core power spectrum needs n_species*n_max <= 128");
         const bool tf32 = mode == kGramTf32x3;
