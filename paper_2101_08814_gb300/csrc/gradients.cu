@@ -136,12 +136,14 @@ __global__ void k_wsym(int S, int L1, int Q, int Qw, int ps_norm, const float* _
 
 // One CTA per centre i:
 //   1. chat = k_l (W + W^T) C from the centre's coefficients (shared memory) and its weight block (global, L1);
-//   2. per chunk of the centre's pairs: stage r_ji, the neighbour's species, f_cut and f_cut';
+//   2. per chunk of the centre's pairs (two CTA barriers per chunk):
 //      radial values (f I, (f I)') per pair (one warp per pair, lanes over (l, n));
 //      Y and dY/du per pair (warp w runs the m = w chains for all pairs, lanes over pairs);
-//      contraction s = sum_lm Y sum_n chat (f I)', w = sum_lm dY/du sum_n chat f I (one warp per pair, lanes over
-//      lm, warp-shuffle reduction);
-//      dE/dr_ji, the force scatter and the virial (one thread per pair).
+//      the last warp stages the next chunk's records (r_ji, the neighbour's species, j, f_cut, f_cut') into the
+//      other of two buffers;
+//      contraction s = sum_lm Y sum_n chat (f I)', w = sum_lm dY/du sum_n chat f I, then dE/dr_ji, the force
+//      scatter and the virial (one warp per pair, lanes over lm, warp-shuffle reduction; F_i and the virial summed
+//      per lane, FP64 across the warps at the end).
 template <int SHAPE = 0>
 __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A) {
     // hyper shape: compile-time constants for the instantiated shapes (kExpShapes), the launch arguments otherwise
@@ -162,24 +164,25 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
     const int QN4 = (QN + 3) & ~3;                            // keeps the float4 arrays 16-byte aligned
     const int Yp = kNlm | 1;                                // odd pitch: conflict-free float4 rows
     float* s_H = reinterpret_cast<float*>(smem_raw);          // chat [Q][n_lm]
-    // the coefficients are needed only by the adjoint, before the pair loop: they share the pair area
-    float* s_C = s_H + QN4;                                   // [Q][n_lm], or [Q][Lp_adj] padded per l (tiled adjoint)
     // per-pair records (r_ji, f_cut, f_cut', species index, j): two buffers that alternate between chunks, so that
-    // the next chunk is staged while the current one is processed
+    // the next chunk is staged while the current one is processed; they come first in the pair area, so that the
+    // first chunk can be staged while the adjoint still reads the coefficients
     float4* s_vec = reinterpret_cast<float4*>(s_H + QN4);     // [2][chunk]
-    float4* s_Yv = s_vec + 2 * chunk;                         // [chunk][Yp]  (Y, dY/dux, dY/duy, dY/duz)
-    float2* s_GD = reinterpret_cast<float2*>(s_Yv + (size_t)chunk * Yp);  // [chunk][F_pad]  (f I, (f I)')
-    float* s_fc = reinterpret_cast<float*>(s_GD + (size_t)chunk * kFpad);  // [2][chunk]
+    float* s_fc = reinterpret_cast<float*>(s_vec + 2 * chunk);  // [2][chunk]
     float* s_dfc = s_fc + 2 * chunk;                          // [2][chunk]
     int* s_spc = reinterpret_cast<int*>(s_dfc + 2 * chunk);   // [2][chunk]
     int* s_j = s_spc + 2 * chunk;                             // [2][chunk]
+    // the coefficients are needed only by the adjoint, before the pair loop: they share the area of Y and G
+    float* s_C = reinterpret_cast<float*>(s_j + 2 * chunk);   // [Q][n_lm], or [Q][Lp_adj] padded per l (tiled adjoint)
+    float4* s_Yv = reinterpret_cast<float4*>(s_C);            // [chunk][Yp]  (Y, dY/dux, dY/duy, dY/duz)
+    float2* s_GD = reinterpret_cast<float2*>(s_Yv + (size_t)chunk * Yp);  // [chunk][F_pad]  (f I, (f I)')
     int* s_lofm = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(s_vec) + A.aux_off);  // [n_lm] l of lm
     int* s_fmap = s_lofm + kNlm;                            // [F_pad]
     __shared__ double red[kGradThreads / 32][12];
     __shared__ int s_sid;
 
     const int i = blockIdx.x;
-    if ((threadIdx.x >> 5) == (blockDim.x >> 5) - 1) {  // the last warp is idle while warp 0 stages the pairs
+    if ((threadIdx.x >> 5) == (blockDim.x >> 5) - 1) {  // the last warp: the centre's structure, for the virial
         const int sid = warp_find_structure(A.offs, A.n_s, i, threadIdx.x & 31);
         if ((threadIdx.x & 31) == 0) s_sid = sid;
     }
@@ -234,13 +237,22 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
         // adjoint as 4 x 4 register tiles of chat_l = Ws_l C_l: C staged with every l block padded to a multiple of
         // 4 columns (zeros), so that tiles load float4 rows of C and of the dense symmetric weights
         const int Lq = kLpAdj;
-        for (int e = tid; e < Q * Lq; e += blockDim.x) s_C[e] = 0.0f;  // padding columns read as zero
-        __syncthreads();
-        for (int q = warp; q < Q; q += nwarps)  // per row: lanes over lm
-            for (int lm = lane; lm < n_lm; lm += 32) {
-                const int l = s_lofm[lm];
-                cp_async4(s_C + q * Lq + exp_lp(l) + (lm - l * l), c + q * n_lm + lm);
-            }
+        // the padding columns of the l blocks (ceil4(2l + 1) - (2l + 1) of them: three for even l, one for odd l)
+        // read as zero; they are disjoint from the copied columns, so the barrier after the copies covers both
+        const int n_padc = 4 * (L1 >> 1) + 3 * (L1 & 1);
+        for (int e = tid; e < Q * n_padc; e += blockDim.x) {
+            const int q = e / n_padc, r = e - q * n_padc;
+            const bool odd = (r & 3) == 3;
+            const int l = 2 * (r >> 2) + (odd ? 1 : 0);
+            s_C[q * Lq + exp_lp(l) + 2 * l + 1 + (odd ? 0 : (r & 3))] = 0.0f;
+        }
+        // lanes over lm, warps over rows; no barrier separates these copies from the prologue, so l is computed
+        // here (once per lm) rather than read from s_lofm, which other warps are still writing
+        for (int lm = lane; lm < n_lm; lm += 32) {
+            const int l = (int)sqrtf((float)lm);  // l with l^2 <= lm < (l + 1)^2
+            const int col = exp_lp(l) + (lm - l * l);
+            for (int q = warp; q < Q; q += nwarps) cp_async4(s_C + q * Lq + col, c + q * n_lm + lm);
+        }
         cp_async_wait_all();
         __syncthreads();
         const int QT = (Q + 3) >> 2;
@@ -340,7 +352,8 @@ __global__ void __launch_bounds__(kGradThreads, 5) k_gradients(const GradArgs A)
             s_dfc[o] = df;
         }
     };
-    __syncthreads();  // the adjoint is done with the staged coefficients, which share the pair area
+    // the first chunk's records do not overlap the coefficients; the first barrier of the loop also ends the adjoint
+    // before Y and G overwrite the coefficients
     if (stager) stage(seg_beg, 0);
     int b = 0;
     for (int64_t pos = seg_beg; pos < seg_end; pos += chunk, b ^= 1) {
@@ -493,15 +506,16 @@ __global__ void k_forces_f64(int64_t n, const float* __restrict__ f32, double* _
         f64[e] = (double)f32[e];
 }
 
-// bytes from the pair area to the small tables: the larger of the pair area and the staged coefficients
+// bytes from the pair area to the small tables: the pair records, then the larger of Y and G and the staged
+// coefficients
 static size_t grad_aux_off(const rascal_ctx* ctx, int chunk, bool tiled) {
     const ExpPlan& P = ctx->plan;
     const size_t QN4 = ((size_t)ctx->Q * ctx->n_lm + 3) / 4 * 4;
     const size_t QL4 = tiled ? ((size_t)ctx->Q * P.Lp + 3) / 4 * 4 : QN4;
     const size_t Yp = (size_t)(ctx->n_lm | 1);
-    const size_t pair_area = sizeof(float4) * chunk * (2 + Yp) + sizeof(float2) * chunk * P.F_pad +
-                             2 * (sizeof(float) * 2 + sizeof(int) * 2) * chunk;  // two buffers of pair records
-    return align_up(std::max(pair_area, sizeof(float) * QL4), 16);
+    const size_t records = 2 * (sizeof(float4) + sizeof(float) * 2 + sizeof(int) * 2) * chunk;  // two buffers
+    const size_t yg = sizeof(float4) * chunk * Yp + sizeof(float2) * chunk * P.F_pad;  // Y and G, or the coefficients
+    return align_up(records + std::max(yg, sizeof(float) * QL4), 16);
 }
 
 // bytes from the pair area to the dense weight block of the per-centre tiled adjoint (behind the small tables)
@@ -621,7 +635,7 @@ extern "C" int rascal_gradients(rascal_ctx* ctx, const rascal_system* sys, const
         for (int l = L1; l < kMaxLMax + 1; ++l) A.adj_pref[l + 1] = A.adj_pref[l];
         A.n_adj_tasks = A.adj_pref[L1];
     }
-    // the largest chunk (<= 32: warp 0 runs the per-pair phase) that keeps five CTAs per SM (48 registers); a
+    // the largest chunk (<= 32: one warp stages a chunk, a pair per lane) that keeps five CTAs per SM (48 registers); a
     // per-centre dE/dp takes the tiled adjoint with one dense l block in shared memory when four CTAs per SM keep a
     // chunk of at least 8 pairs, else the per-element adjoint
     int chunk = 32;
