@@ -31,10 +31,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + written) per environment of the fused pair kernel with the FP32 power spectrum
 # (k_expansion<kGramSimt> in its compiled instance for the batch hypers, PACKED layout) on the batch workload's recipe,
-# from one ncu capture of a 96-cell case: (7.635 MB + 843.993 MB) / 13 434 environments (dram__bytes_read.sum +
+# from one ncu capture of a 96-cell case: (7.676 MB + 843.154 MB) / 13 434 environments (dram__bytes_read.sum +
 # dram__bytes_write.sum). Scaled to a full launch by the environments it processes; valid only while that kernel is
 # unchanged.
-FUSED_FP32_TRAFFIC_PER_ENV = (7.635e6 + 843.993e6) / 13434
+FUSED_FP32_TRAFFIC_PER_ENV = (7.676e6 + 843.154e6) / 13434
 
 WORKLOADS = {
     "batch": "512 periodic cubic cells, 64-216 atoms each (uniform), 0.05 atoms/A^3, 4 species uniform, d_min 1.8 A; "
