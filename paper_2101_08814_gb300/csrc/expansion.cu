@@ -223,72 +223,76 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
 
         for (int pos = 0; pos < seg_len; pos += chunk) {  // pair offsets relative to the centre's segment
             const int nc = min(chunk, seg_len - pos);
-            if (chunk <= 32) {
-                // warp 0 stages the chunk, one pair per lane, and lists it by species straight from its registers
-                if (warp == 0) {
-                    int a = -2;  // lanes without a pair match no species
-                    if (lane < nc) {
-                        const float4 v = seg_rij[pos + lane];
-                        const int j = seg_j[pos + lane];
-                        const int lab = A.species[j];
-                        a = (lab >= 0 && lab < 256) ? A.lut[lab] : -1;
-                        if (a < 0) atomicOr(A.flags, kFlagSpecies);
-                        if (!(v.w > 1e-6f)) a = -1;  // coincident atoms are flagged by the neighbour search
-                        s_vec[lane] = v;
-                        s_fc[lane] = cutoff_fp32(v.w, A.r_cut, A.width);
-                    }
-                    int base = 0;
-                    #pragma unroll 1
-                    for (int ga = 0; ga < na; ++ga) {
-                        if (lane == 0) s_start[ga] = base;
-                        const unsigned m = __ballot_sync(0xffffffffu, a == a0 + ga);
-                        if (a == a0 + ga) s_list[base + __popc(m & ((1u << lane) - 1u))] = lane;
-                        base += __popc(m);
-                    }
-                    if (lane == 0) s_start[na] = base;
+            // staging: r_ji and f_cut per pair. With one species round (SIMT Gram forms) the rows of Y and G are
+            // indexed by pair position, and warp 0 lists the chunk's pairs by species (s_list, s_start) during the
+            // radial and Y phases, which then do not wait for the neighbours' species; with several rounds the list
+            // comes first and only the round's pairs get rows (so too in the tensor-core forms, where the two
+            // values warp 0 would hold through the phase cost more than the wait: 2.98 against 2.91 ms in BF16)
+            const bool early = kCT && kRounds == 1;
+            int lab = -1;  // chunk <= 32: the neighbour's species label, held by lane p of warp 0
+            float vw = 0.0f;
+            auto list_pairs = [&]() {  // warp 0
+                int a = -2;  // lanes without a pair match no species
+                if (chunk <= 32 && lane < nc) {
+                    a = (lab >= 0 && lab < 256) ? A.lut[lab] : -1;
+                    if (a < 0) atomicOr(A.flags, kFlagSpecies);
+                    if (!(vw > 1e-6f)) a = -1;  // coincident atoms are flagged by the neighbour search
                 }
-            } else {
-            #pragma unroll 1
-            for (int t = tid; t < nc; t += blockDim.x) {
-                const float4 v = seg_rij[pos + t];
-                const int j = seg_j[pos + t];
-                const int lab = A.species[j];
-                int a = (lab >= 0 && lab < 256) ? A.lut[lab] : -1;
-                if (a < 0) atomicOr(A.flags, kFlagSpecies);
-                if (!(v.w > 1e-6f)) a = -1;  // coincident atoms are flagged by the neighbour search
-                s_vec[t] = v;
-                s_spc[t] = a;
-                s_fc[t] = cutoff_fp32(v.w, A.r_cut, A.width);
-            }
-            __syncthreads();
-            if (warp == 0) {
                 int base = 0;
                 #pragma unroll 1
                 for (int ga = 0; ga < na; ++ga) {
-                    const int a = a0 + ga;
                     if (lane == 0) s_start[ga] = base;
                     #pragma unroll 1
                     for (int p0 = 0; p0 < nc; p0 += 32) {
                         const int p = p0 + lane;
-                        const bool mine = (p < nc) && (s_spc[p] == a);
+                        const bool mine = chunk <= 32 ? (a == a0 + ga) : (p < nc && s_spc[p] == a0 + ga);
                         const unsigned m = __ballot_sync(0xffffffffu, mine);
                         if (mine) s_list[base + __popc(m & ((1u << lane) - 1u))] = p;
                         base += __popc(m);
                     }
                 }
                 if (lane == 0) s_start[na] = base;
+            };
+            if (chunk <= 32) {
+                if (warp == 0) {
+                    if (lane < nc) {
+                        const float4 v = seg_rij[pos + lane];
+                        const int j = seg_j[pos + lane];
+                        s_vec[lane] = v;
+                        s_fc[lane] = cutoff_fp32(v.w, A.r_cut, A.width);
+                        vw = v.w;
+                        lab = A.species[j];
+                    }
+                    if (!early) list_pairs();
+                }
+            } else {
+            #pragma unroll 1
+            for (int t = tid; t < nc; t += blockDim.x) {
+                const float4 v = seg_rij[pos + t];
+                const int j = seg_j[pos + t];
+                const int lb = A.species[j];
+                int a = (lb >= 0 && lb < 256) ? A.lut[lb] : -1;
+                if (a < 0) atomicOr(A.flags, kFlagSpecies);
+                if (!(v.w > 1e-6f)) a = -1;  // coincident atoms are flagged by the neighbour search
+                s_vec[t] = v;
+                s_spc[t] = a;
+                s_fc[t] = cutoff_fp32(v.w, A.r_cut, A.width);
+            }
+            if (!early) {
+                __syncthreads();
+                if (warp == 0) list_pairs();
             }
             }
             __syncthreads();
-            const int n_list = s_start[na];
-            // Y_lm: warp w runs the chains of m = w, w + nwarps, ... with the lanes over the listed pairs, so the
-            // recurrence coefficients and the loop bounds are uniform across the warp
+            const int n_rows = early ? nc : s_start[na];
+            // Y_lm: warp w runs the chains of m = w, w + nwarps, ... with the lanes over the rows, so the recurrence
+            // coefficients and the loop bounds are uniform across the warp
             #pragma unroll 1
             for (int m = warp; m < L1; m += nwarps) {
                 const float km = c_ylm_K[m];
                 #pragma unroll 1
-                for (int q = lane; q < n_list; q += 32) {
-                    const float4 v = s_vec[s_list[q]];
+                for (int q = lane; q < n_rows; q += 32) {
+                    const float4 v = s_vec[early ? q : s_list[q]];
                     const float inv_r = 1.0f / v.w;
                     const float x = v.x * inv_r, y = v.y * inv_r, z = v.z * inv_r;
                     float cm = 1.0f, sm = 0.0f;
@@ -324,10 +328,10 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     }
                 }
             }
-            // radial values G = f_cut I^o_nl: one warp per listed pair, lanes over padded (l, n); the warps without a
-            // Y chain take the first pairs
-            for (int q = nwarps - 1 - warp; q < n_list; q += nwarps) {
-                const int p = s_list[q];
+            // radial values G = f_cut I^o_nl: one warp per row, lanes over padded (l, n); the warps without a Y chain
+            // take the first rows
+            for (int q = nwarps - 1 - warp; q < n_rows; q += nwarps) {
+                const int p = early ? q : s_list[q];
                 const float fc = s_fc[p];
                 float* grow = s_G + q * kFpad;
                 if (A.pre_G) {  // per-pair values (EXACT / MLP radial modes)
@@ -350,12 +354,14 @@ __global__ void __launch_bounds__(512, 3) k_expansion(const ExpArgs A) {
                     }
                 }
             }
+            if (early && warp == 0) list_pairs();
             __syncthreads();
             if (active) {
                 const int beg = s_start[g], end = s_start[g + 1];
                 for (int q = beg; q < end; ++q) {
-                    const float4 gv = *reinterpret_cast<const float4*>(s_G + q * kFpad + g_off);
-                    const float4 yv = *reinterpret_cast<const float4*>(s_Y + q * kLy + y_off);
+                    const int row = early ? s_list[q] : q;
+                    const float4 gv = *reinterpret_cast<const float4*>(s_G + row * kFpad + g_off);
+                    const float4 yv = *reinterpret_cast<const float4*>(s_Y + row * kLy + y_off);
                     const uint64_t y01 = f2_pack(yv.x, yv.y), y23 = f2_pack(yv.z, yv.w);
                     const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
 #pragma unroll
