@@ -31,10 +31,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + written) per environment of the fused pair kernel with the FP32 power spectrum
 # (k_expansion<kGramSimt> in its compiled instance for the batch hypers, PACKED layout) on the batch workload's recipe,
-# from one ncu capture of a 96-cell case: (7.676 MB + 843.154 MB) / 13 434 environments (dram__bytes_read.sum +
-# dram__bytes_write.sum). Scaled to a full launch by the environments it processes; valid only while that kernel is
-# unchanged.
-FUSED_FP32_TRAFFIC_PER_ENV = (7.676e6 + 843.154e6) / 13434
+# from one ncu capture of a 96-cell case (dram__bytes_read.sum + dram__bytes_write.sum), scaled to a full launch by
+# the environments it processes; valid only while that kernel is unchanged, None (reported as null) otherwise. The
+# last capture, (7.676 MB + 843.154 MB) / 13 434 environments, is of the kernel before its pair phase indexed the Y
+# and G rows by pair position.
+FUSED_FP32_TRAFFIC_PER_ENV = None
 
 WORKLOADS = {
     "batch": "512 periodic cubic cells, 64-216 atoms each (uniform), 0.05 atoms/A^3, 4 species uniform, d_min 1.8 A; "
@@ -649,7 +650,7 @@ def run_ours(args):
                          and args.layout == "packed" and args.radial == "spline" and sel is None)
         roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": (achieved / peak) if achieved else None,
-                    "traffic": FUSED_FP32_TRAFFIC_PER_ENV * N if traffic_known else None,
+                    "traffic": FUSED_FP32_TRAFFIC_PER_ENV * N if traffic_known and FUSED_FP32_TRAFFIC_PER_ENV else None,
                     "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
     if radial_info.get("check_error"):
         radial_info["c_err_vs_exact_fp64"] = coefficient_error(calc, ds, coeffs, rg, args)
