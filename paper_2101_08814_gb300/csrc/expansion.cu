@@ -6,10 +6,12 @@
 // One CTA per centre i. The centre's CSR segment of pairs is processed in chunks staged in shared memory:
 //   1. stage r_ji (float4 x, y, z, r), the neighbour's species and f_cut(r) for the chunk;
 //   2. list the chunk's pairs by species (warp ballots, so the order is deterministic);
-//   3. per listed pair: Y_lm by the Cartesian recurrence (one thread per (pair, m) chain) and the radial values
-//      G_nl = f_cut(r) I^o_nl(r) from the FP32 cubic spline table (one warp per pair, lanes over (l, n));
+//   3. per pair: Y_lm by the Cartesian recurrence (one thread per (pair, m) chain) and the radial values
+//      G_nl = f_cut(r) I^o_nl(r) from the FP32 cubic spline table (one warp per pair, lanes over (l, n)). With one
+//      species round (the SIMT Gram forms) steps 2 and 3 run side by side, the rows of Y and G indexed by pair
+//      position; otherwise step 3 follows step 2 and covers only the round's listed pairs;
 //   4. accumulate: each thread owns a 4(n) x 4(m) register tile of one l and one species and adds the outer
-//      product G_{l, n-tile} x Y_{l, m-tile} for every pair of its species (16 FMAs per two float4 loads).
+//      product G_{l, n-tile} x Y_{l, m-tile} for every listed pair of its species (16 FMAs per two float4 loads).
 // The segment reduction happens in registers; no atomics. The tiles are stored to the centre's block of c in global
 // memory and, when the power spectrum is fused, also into shared memory, where the Gram runs without c ever being
 // read back from HBM:
@@ -17,7 +19,7 @@
 //   kGramBf16    tcgen05 MMA, BF16 operands, FP32 accumulators in TMEM (tcgen05.cuh);
 //   kGramTf32x3  tcgen05 MMA, TF32 hi/lo split, three MMAs per K step (FP32-grade).
 // The Gram output is staged per group of l values in the (then free) pair-staging buffers and written to global
-// memory with coalesced stores.
+// memory by bulk copies.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -65,7 +67,7 @@ struct ExpArgs {
     int gram_off;                   // bytes: CT (SIMT, behind the pair area) or operand tiles (tensor cores, at 0)
     int pair_off;                   // bytes: start of the pair staging area (behind the tiles in tensor-core mode)
     int stage_floats;               // capacity of the staging area (aliases the pair buffers)
-    int p_half;                     // SIMT: the staging area holds two halves of p_half floats
+    int p_half;                     // SIMT: the first staging half holds p_half floats, the second the rest
     int n_groups;
     int g_lo[kMaxGroups], g_hi[kMaxGroups];      // l range [g_lo, g_hi) of each output group
     const int* ps_tasks;            // SIMT tasks, l descending
