@@ -61,6 +61,8 @@ def parse_args(argv=None):
                     help="rascal_spherical_expansion + rascal_power_spectrum instead of the fused rascal_soap")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="host seconds of oracle work that --impl reference spreads over its warm-up and timed steps")
     ap.add_argument("--cpu-seconds", type=float, default=24.0,
                     help="host seconds of oracle work in the CPU baseline, split over its three modes")
     ap.add_argument("--structures", type=int, default=512, help="cells in the batch workload (profiling cases)")
@@ -437,7 +439,7 @@ def run_reference(args):
         t0 = time.perf_counter()
         probe = sum(pool.map(_pool_task, [order[2 + 2 * k:4 + 2 * k] for k in range(cores)], chunksize=1))
         per = (time.perf_counter() - t0) / probe  # wall seconds per centre with every core busy
-        budget = 150.0
+        budget = args.ref_seconds
         per_step = max(cores, int(budget / max(per, 1e-6) / (args.steps + args.warmup)))
         cursor = 2 + 2 * cores
 
