@@ -142,6 +142,18 @@ int rascal_sync(rascal_ctx* ctx);
  * usable throughout. Returns RASCAL_E_ARG for a NULL context. */
 int rascal_debug_wait_timeout(rascal_ctx* ctx, unsigned polls);
 
+/* Test hooks for tables the library builds on the host (no context and no GPU needed; no counterpart in the paper).
+ * rascal_debug_gauss_legendre: the n Gauss-Legendre points x[n] (ascending) and weights w[n] on [0, X] on which
+ *   the DVR radial basis (Eq. rad-int-dvr) places its functions, in FP64; n in [1, 64] and X > 0, else
+ *   RASCAL_E_ARG.
+ * rascal_debug_real_coupling: the table R[mu][m1][m2], (2 lambda + 1) (2 l1 + 1) (2 l2 + 1) float32 values, that
+ *   couples the real-harmonic coefficients of ranks l1 and l2 (the basis of rascal_spherical_expansion, index
+ *   m + l) to the real rank-lambda equivariant of rascal_lambda_soap (Eq. body-order-x at nu = 2: Clebsch-Gordan
+ *   coefficients carried into the real basis in FP64 and rounded once). Needs l1, l2 <= 15,
+ *   |l1 - l2| <= lambda <= l1 + l2 and l1 + l2 + lambda even, else RASCAL_E_ARG. The caller owns the outputs. */
+int rascal_debug_gauss_legendre(int n, double X, double* x, double* w);
+int rascal_debug_real_coupling(int l1, int l2, int lambda, float* R);
+
 /* Periodic neighbour list (Appendix B). For every atom i (all structures, in atom order) the pairs (j, n) with
  * |r_j - r_i + n H| < r_cut, (j, n) != (i, 0), sorted by (j, n1, n2, n3). The inclusion test is bit-exact with
  * the FP64 definition d = (r_j - r_i) + ((n1 h1 + n2 h2) + n3 h3), d.d = (dx dx + dy dy) + dz dz < r_cut^2.

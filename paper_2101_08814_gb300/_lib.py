@@ -119,6 +119,8 @@ _SIGNATURES = {
     "rascal_lambda_soap_size": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "rascal_debug_pair_gradients": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "rascal_debug_wait_timeout": (C.c_int, [C.c_void_p, C.c_uint]),
+    "rascal_debug_gauss_legendre": (C.c_int, [C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
+    "rascal_debug_real_coupling": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "rascal_lambda_soap": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p]),
     "rascal_gpr_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(System), C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),

@@ -432,6 +432,13 @@ extern "C" const char* rascal_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" long long rascal_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+extern "C" int rascal_debug_gauss_legendre(int n, double X, double* x, double* w) {
+    clear_error();
+    if (n < 1 || n > 64 || !(X > 0.0) || !x || !w) return set_error(RASCAL_E_ARG, "n in [1, 64], X > 0, non-NULL outputs");
+    gauss_legendre(n, X, x, w);
+    return RASCAL_OK;
+}
+
 extern "C" void rascal_destroy(rascal_ctx* ctx) {
     if (!ctx) return;
     cudaFree(ctx->d_table);

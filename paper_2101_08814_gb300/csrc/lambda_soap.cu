@@ -288,6 +288,17 @@ extern "C" int rascal_lambda_soap_size(const rascal_ctx* ctx, int lambda, int* n
     return RASCAL_OK;
 }
 
+extern "C" int rascal_debug_real_coupling(int l1, int l2, int lambda, float* R) {
+    clear_error();
+    if (l1 < 0 || l2 < 0 || l1 > kMaxLMax || l2 > kMaxLMax || lambda < std::abs(l1 - l2) || lambda > l1 + l2 ||
+        ((l1 + l2 + lambda) & 1) || !R)
+        return set_error(RASCAL_E_ARG, "l1, l2 <= %d, |l1 - l2| <= lambda <= l1 + l2, l1 + l2 + lambda even", kMaxLMax);
+    std::vector<float> t;
+    if (!real_table(l1, l2, lambda, t)) return set_error(RASCAL_E_UNSUPPORTED, "coupling is not real");
+    std::memcpy(R, t.data(), t.size() * sizeof(float));
+    return RASCAL_OK;
+}
+
 extern "C" int rascal_lambda_soap(rascal_ctx* ctx, int64_t n_centres, const float* d_coeffs, int lambda, float* d_out) {
     clear_error();
     if (!ctx) return set_error(RASCAL_E_ARG, "NULL context");
